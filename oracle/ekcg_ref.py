@@ -1,0 +1,576 @@
+"""FP64 CPU oracle for the s-step enlarged Krylov subspace CG methods.
+
+TEST INFRASTRUCTURE ONLY.  Only the tests, the smoke check of `__graft_entry__` and the
+CPU-baseline leg of `bench.py` may import this module.  The CUDA library never calls it,
+shares no code with it, and does not fall back to it.
+
+Plain, slow, obviously-correct NumPy/SciPy code in float64.  Each function follows the
+paper (Moufawad, "Numerical Stability of s-step Enlarged Krylov Subspace Conjugate Gradient
+methods", arXiv:1804.10629) step by step; the section / algorithm / equation it follows is
+named in its docstring.  Library primitives used as steps: sparse matrix x dense block
+(scipy.sparse), dense matrix products (NumPy/BLAS), Householder QR (numpy.linalg.qr) and
+triangular solves (scipy.linalg.solve_triangular).
+
+Everything works in the caller's (natural) row order.  The splitting operator T uses the
+partition array directly: T(r)[i, part[i]] = r[i].  The domain permutation of Section 4
+(rows reordered so that domains are contiguous) is a storage choice; `domain_perm` gives
+the permutation the GPU library must reproduce.
+
+Readings where the paper is silent or refers to the author's thesis (all listed in
+the design doc too):
+  * CGS2 against Q (thesis Alg. 18, not printed): two passes of C = Q^T (A W),
+    W <- W - Q C, with A W carried along: AW <- AW - (AQ) C.
+  * A-CholQR (thesis Alg. 21): G = W^T (A W) = R^T R (upper Cholesky of the upper
+    triangle of G), W <- W R^{-1}, AW <- AW R^{-1}.
+  * Pre-CholQR (thesis Alg. 23): thin Euclidean QR W = Z S with diag(S) > 0 first, then
+    A-CholQR of Z (AZ = AW S^{-1}).
+  * A W is carried by the same linear recurrences as W, so each new block costs exactly one
+    sparse product; the next candidate block A W_{j-1} is the carried A W_{j-1}.
+    `explicit_AW=True` recomputes A W with a sparse product after every step instead.
+  * Missing window blocks in the first iterations (W_{j-2} for j < 3) are skipped.
+  * Stopping rule: while rho > tol*rho0 and iterations < maxit, rho = ||r_k||_2 of the
+    recursively updated residual, checked once per s-step iteration.
+  * Breakdown: a Cholesky pivot d_i <= breakdown_tol * |G_ii| (or a non-finite one) stops
+    the solve with status BREAKDOWN and the current iterate.
+  * CA SRE-CG window: the last (s+1)t basis vectors; CA SRE-CG2 / (CA) MSDO-CG: all.
+  * Inside a CA block V the columns are power-major: column p*t + i belongs to A^p W_i.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+from typing import List, Optional
+
+import numpy as np
+import scipy.linalg as sla
+import scipy.sparse as sp
+
+OK = 0
+MAXIT = 1
+BREAKDOWN = -3
+
+VARIANTS = ("sre", "sre2", "msdo")
+BASES = ("sstep", "ca5", "ca7")
+ORTHS = ("acholqr", "precholqr")
+
+
+class Breakdown(Exception):
+    """Raised when a Cholesky pivot fails the breakdown rule."""
+
+
+@dataclasses.dataclass
+class Result:
+    x: np.ndarray
+    iters: int
+    hist: List[float]
+    status: int
+    xs: List[np.ndarray] = dataclasses.field(default_factory=list)       # x_0, x_1, ...
+    orth_loss: List[float] = dataclasses.field(default_factory=list)     # max|Q^T A Q - I|
+    pg_loss: List[float] = dataclasses.field(default_factory=list)       # ||V_k^T r_k|| / ||r_k||
+    residuals: List[np.ndarray] = dataclasses.field(default_factory=list)  # r_0, r_1, ...
+    basis: Optional[np.ndarray] = None   # stored Q at exit (full-history methods, record=True)
+    spmm_count: int = 0
+
+
+# ----------------------------------------------------------------------------------------
+# Domain decomposition: permutation and the splitting operator T (Section 2, Section 4)
+# ----------------------------------------------------------------------------------------
+
+def domain_perm(part: np.ndarray) -> np.ndarray:
+    """Row permutation that makes the t domains contiguous (Section 4: the matrix is
+    reordered by the k-way partition).  Stable: rows keep their natural order inside a
+    domain.  perm[i] = original row placed at position i."""
+    return np.argsort(np.asarray(part), kind="stable").astype(np.int64)
+
+
+def split_T(r: np.ndarray, part: np.ndarray, t: int) -> np.ndarray:
+    """T(r) of Section 2: the n x t matrix whose column d is r restricted to domain d
+    (the projection of r on the d-th domain), zero elsewhere."""
+    n = r.shape[0]
+    T = np.zeros((n, t))
+    T[np.arange(n), np.asarray(part)] = r
+    return T
+
+
+# ----------------------------------------------------------------------------------------
+# A-orthonormalisation (Section 3.1 and Section 4: CGS2 + A-CholQR or Pre-CholQR)
+# ----------------------------------------------------------------------------------------
+
+def cholesky_upper(G: np.ndarray, breakdown_tol: float) -> np.ndarray:
+    """Upper Cholesky factor R (G = R^T R) from the upper triangle of G, right-looking.
+    Breakdown rule: pivot d_i <= breakdown_tol*|G_ii| or non-finite."""
+    m = G.shape[0]
+    S = np.triu(np.array(G, dtype=np.float64))
+    R = np.zeros((m, m))
+    for i in range(m):
+        d = S[i, i]
+        if not np.isfinite(d) or d <= breakdown_tol * abs(G[i, i]):
+            raise Breakdown(f"pivot {i}: {d!r} vs G_ii {G[i, i]!r}")
+        R[i, i] = math.sqrt(d)
+        R[i, i + 1:] = S[i, i + 1:] / R[i, i]
+        S[i + 1:, i + 1:] -= np.triu(np.outer(R[i, i + 1:], R[i, i + 1:]))
+    return R
+
+
+def right_solve_upper(W: np.ndarray, R: np.ndarray) -> np.ndarray:
+    """W R^{-1} for upper-triangular R (solves X R = W)."""
+    return sla.solve_triangular(R, W.T, trans="T", lower=False).T
+
+
+def a_cholqr(W, AW, breakdown_tol):
+    """A-CholQR: G = W^T A W = R^T R, W <- W R^{-1} (and A W <- A W R^{-1})."""
+    G = W.T @ AW
+    R = cholesky_upper(G, breakdown_tol)
+    return right_solve_upper(W, R), right_solve_upper(AW, R)
+
+
+def pre_cholqr(W, AW, breakdown_tol):
+    """Pre-CholQR: Euclidean thin QR W = Z S (diag(S) > 0), then A-CholQR of Z."""
+    Z, S = np.linalg.qr(W)
+    sgn = np.where(np.diag(S) < 0, -1.0, 1.0)
+    Z = Z * sgn
+    S = S * sgn[:, None]
+    dS = np.diag(S) ** 2
+    gdiag = np.einsum("ij,ij->j", W, W)
+    if not np.all(np.isfinite(dS)) or np.any(dS <= breakdown_tol * gdiag):
+        raise Breakdown("Euclidean QR pivot")
+    return a_cholqr(Z, right_solve_upper(AW, S), breakdown_tol)
+
+
+def cgs2_against(W, AW, Q, AQ):
+    """CGS2 A-orthonormalisation of W against the A-orthonormal Q: two passes of
+    C = Q^T (A W), W <- W - Q C, A W <- A W - (A Q) C."""
+    for _ in range(2):
+        C = Q.T @ AW
+        W = W - Q @ C
+        AW = AW - AQ @ C
+    return W, AW
+
+
+# ----------------------------------------------------------------------------------------
+# Helpers shared by the solvers
+# ----------------------------------------------------------------------------------------
+
+class _Ctx:
+    """Per-solve state: the operator, options and bookkeeping."""
+
+    def __init__(self, A, part, t, orth, breakdown_tol, explicit_AW, record):
+        self.A = A.to_scipy() if hasattr(A, "to_scipy") else sp.csr_matrix(A)
+        self.part = np.asarray(part)
+        self.t = t
+        self.orth = orth
+        self.tol_bd = breakdown_tol
+        self.explicit = explicit_AW
+        self.record = record
+        self.spmm = 0
+
+    def matmul(self, W):
+        self.spmm += 1
+        return self.A @ W
+
+    def self_orth(self, W, AW):
+        if self.orth == "acholqr":
+            W, AW = a_cholqr(W, AW, self.tol_bd)
+        elif self.orth == "precholqr":
+            W, AW = pre_cholqr(W, AW, self.tol_bd)
+        else:
+            raise ValueError(self.orth)
+        if self.explicit:
+            AW = self.A @ W
+        return W, AW
+
+    def against(self, W, AW, blocks):
+        if isinstance(blocks, _Basis):
+            if blocks.m == 0:
+                return W, AW
+            Q, AQ = blocks.Q, blocks.AQ
+        else:
+            if not blocks:
+                return W, AW
+            Q = np.hstack([b[0] for b in blocks])
+            AQ = np.hstack([b[1] for b in blocks])
+        W, AW = cgs2_against(W, AW, Q, AQ)
+        if self.explicit:
+            AW = self.A @ W
+        return W, AW
+
+
+class _Basis:
+    """Stored basis vectors Q and their products A Q as contiguous n x m arrays (grown by
+    doubling), so that a full-history solve does not re-concatenate Q every step."""
+
+    def __init__(self, n):
+        self.n = n
+        self.m = 0
+        self._Q = np.empty((n, 0))
+        self._AQ = np.empty((n, 0))
+
+    def append(self, W, AW):
+        w = W.shape[1]
+        if self.m + w > self._Q.shape[1]:
+            cap = max(2 * self._Q.shape[1], self.m + w, 16)
+            Q = np.empty((self.n, cap))
+            AQ = np.empty((self.n, cap))
+            Q[:, :self.m] = self._Q[:, :self.m]
+            AQ[:, :self.m] = self._AQ[:, :self.m]
+            self._Q, self._AQ = Q, AQ
+        self._Q[:, self.m:self.m + w] = W
+        self._AQ[:, self.m:self.m + w] = AW
+        self.m += w
+
+    @property
+    def Q(self):
+        return self._Q[:, :self.m]
+
+    @property
+    def AQ(self):
+        return self._AQ[:, :self.m]
+
+    def blocks(self, t):
+        return [(self.Q[:, i:i + t], self.AQ[:, i:i + t]) for i in range(0, self.m, t)]
+
+
+def _orth_loss_arrays(Q, AQ):
+    return float(np.max(np.abs(Q.T @ AQ - np.eye(Q.shape[1]))))
+
+
+def _orth_loss(blocks):
+    if isinstance(blocks, _Basis):
+        return _orth_loss_arrays(blocks.Q, blocks.AQ)
+    Q = np.hstack([b[0] for b in blocks])
+    AQ = np.hstack([b[1] for b in blocks])
+    return _orth_loss_arrays(Q, AQ)
+
+
+def _start(A, b, x0):
+    Asp = A.to_scipy() if hasattr(A, "to_scipy") else sp.csr_matrix(A)
+    x = np.zeros_like(b, dtype=np.float64) if x0 is None else np.array(x0, dtype=np.float64)
+    r = b - Asp @ x
+    return x, r, float(np.linalg.norm(r))
+
+
+def _update(ctx, res, x, r, V, AV):
+    """Lines 'alpha = V^T r_{k-1}; x_k = x_{k-1} + V alpha; r_k = r_{k-1} - AV alpha'."""
+    alpha = V.T @ r
+    x = x + V @ alpha
+    r = r - AV @ alpha
+    return x, r, float(np.linalg.norm(r))
+
+
+def _finish(res, x, rho, rho0, tol, k):
+    res.x = x
+    res.iters = k - 1
+    if res.status != BREAKDOWN:
+        res.status = OK if rho <= tol * rho0 else MAXIT
+    return res
+
+
+def _record(ctx, res, x, r, V=None, blocks=None):
+    if not ctx.record:
+        return
+    res.xs.append(x.copy())
+    res.residuals.append(r.copy())
+    if V is not None:
+        nr = np.linalg.norm(r)
+        res.pg_loss.append(float(np.linalg.norm(V.T @ r) / (nr if nr > 0 else 1.0)))
+    if blocks is not None and (not isinstance(blocks, list) or blocks):
+        res.orth_loss.append(_orth_loss(blocks))
+
+
+# ----------------------------------------------------------------------------------------
+# Classical CG (Section 2)
+# ----------------------------------------------------------------------------------------
+
+def cg(A, b, x0=None, tol=1e-8, maxit=10000, record=False) -> Result:
+    """Conjugate Gradient as stated in Section 2: p_1 = r_0, p_k = r_{k-1} + beta_k p_{k-1},
+    alpha_k = ||r_{k-1}||^2 / ||p_k||_A^2, beta_k = ||r_{k-1}||^2 / ||r_{k-2}||^2,
+    x_k = x_{k-1} + alpha_k p_k, r_k = r_{k-1} - alpha_k A p_k; same stopping rule as the
+    enlarged algorithms (rho = ||r_k||_2 > tol*rho_0 and k < k_max)."""
+    Asp = A.to_scipy() if hasattr(A, "to_scipy") else sp.csr_matrix(A)
+    x, r, rho0 = _start(A, b, x0)
+    res = Result(x=x, iters=0, hist=[rho0], status=OK)
+    if record:
+        res.xs.append(x.copy())
+        res.residuals.append(r.copy())
+    rho, k = rho0, 1
+    p = None
+    rr_prev = None
+    kmax = maxit + 1
+    while rho > tol * rho0 and k < kmax:
+        rr = float(r @ r)
+        p = r.copy() if k == 1 else r + (rr / rr_prev) * p
+        Ap = Asp @ p
+        alpha = rr / float(p @ Ap)
+        x = x + alpha * p
+        r = r - alpha * Ap
+        rr_prev = rr
+        rho = float(np.linalg.norm(r))
+        res.hist.append(rho)
+        if record:
+            res.xs.append(x.copy())
+            res.residuals.append(r.copy())
+        k += 1
+    return _finish(res, x, rho, rho0, tol, k)
+
+
+# ----------------------------------------------------------------------------------------
+# s-step SRE-CG (Algorithm 4) and s-step SRE-CG2 (Algorithm 3)
+# ----------------------------------------------------------------------------------------
+
+def sstep_sre_cg(A, b, part, t, s, tol=1e-8, maxit=1000, x0=None, orth="acholqr",
+                 full_history=False, breakdown_tol=1e-14, explicit_AW=False,
+                 record=False) -> Result:
+    """s-step SRE-CG (Algorithm 4); with full_history=True, s-step SRE-CG2 (Algorithm 3).
+
+    Iteration k builds s blocks W_j..W_{j+s-1}, j = (k-1)s+1.  W_1 = T(r_0) is only
+    A-orthonormalised against itself; every later W_j = A W_{j-1} is A-orthonormalised
+    against W_{j-2}, W_{j-1} (Alg. 4) or against all previous blocks (Alg. 3), then against
+    itself.  Then alpha = V^T r_{k-1}, x_k = x_{k-1} + V alpha, r_k = r_{k-1} - A V alpha.
+    """
+    ctx = _Ctx(A, part, t, orth, breakdown_tol, explicit_AW, record)
+    x, r, rho0 = _start(A, b, x0)
+    res = Result(x=x, iters=0, hist=[rho0], status=OK)
+    _record(ctx, res, x, r)
+    r0 = r.copy()
+    window = []                      # Alg. 4: (W, AW) of the last two blocks
+    full = _Basis(b.shape[0])        # Alg. 3: all blocks
+    last = None                      # (W_{j-1}, A W_{j-1})
+    rho, k = rho0, 1
+    kmax = maxit + 1
+    try:
+        while rho > tol * rho0 and k < kmax:
+            Vb = []
+            for i in range(s):
+                if k == 1 and i == 0:
+                    W = split_T(r0, ctx.part, t)
+                    AW = ctx.matmul(W)
+                else:
+                    W = last[1]                            # W_j = A W_{j-1}
+                    AW = ctx.matmul(W)
+                    W, AW = ctx.against(W, AW, full if full_history else window)
+                W, AW = ctx.self_orth(W, AW)
+                last = (W, AW)
+                Vb.append(last)
+                if full_history:
+                    full.append(W, AW)
+                else:
+                    window = (window + [last])[-2:]
+            V = np.hstack([v[0] for v in Vb])
+            AV = np.hstack([v[1] for v in Vb])
+            x, r, rho = _update(ctx, res, x, r, V, AV)
+            res.hist.append(rho)
+            _record(ctx, res, x, r, V, full if full_history else Vb)
+            k += 1
+    except Breakdown:
+        res.status = BREAKDOWN
+    res.spmm_count = ctx.spmm
+    if record and full_history:
+        res.basis = full.Q.copy()
+    return _finish(res, x, rho, rho0, tol, k)
+
+
+def sstep_sre_cg2(*args, **kw) -> Result:
+    """s-step SRE-CG2 (Algorithm 3): Algorithm 4 with orthonormalisation against all Q."""
+    kw["full_history"] = True
+    return sstep_sre_cg(*args, **kw)
+
+
+# ----------------------------------------------------------------------------------------
+# s-step MSDO-CG (Algorithm 6, modified enlarged Krylov subspace of Section 3.2)
+# ----------------------------------------------------------------------------------------
+
+def sstep_msdo_cg(A, b, part, t, s, tol=1e-8, maxit=1000, x0=None, orth="acholqr",
+                  breakdown_tol=1e-14, explicit_AW=False, record=False) -> Result:
+    """s-step MSDO-CG (Algorithm 6).  Iteration k: W_1 = T(r_{k-1}) A-orthonormalised
+    against Q (k > 1) and itself; W_{i+1} = A W_i against Q and itself, i = 1..s-1; every
+    block joins V and Q.  Then alpha = V^T r_{k-1} and the x / r updates."""
+    ctx = _Ctx(A, part, t, orth, breakdown_tol, explicit_AW, record)
+    x, r, rho0 = _start(A, b, x0)
+    res = Result(x=x, iters=0, hist=[rho0], status=OK)
+    _record(ctx, res, x, r)
+    Qb = _Basis(b.shape[0])
+    rho, k = rho0, 1
+    kmax = maxit + 1
+    try:
+        while rho > tol * rho0 and k < kmax:
+            Vb = []
+            W = split_T(r, ctx.part, t)
+            AW = ctx.matmul(W)
+            W, AW = ctx.against(W, AW, Qb)
+            W, AW = ctx.self_orth(W, AW)
+            Vb.append((W, AW))
+            Qb.append(W, AW)
+            for i in range(1, s):
+                W = Vb[-1][1]                              # W_{i+1} = A W_i
+                AW = ctx.matmul(W)
+                W, AW = ctx.against(W, AW, Qb)
+                W, AW = ctx.self_orth(W, AW)
+                Vb.append((W, AW))
+                Qb.append(W, AW)
+            V = np.hstack([v[0] for v in Vb])
+            AV = np.hstack([v[1] for v in Vb])
+            x, r, rho = _update(ctx, res, x, r, V, AV)
+            res.hist.append(rho)
+            _record(ctx, res, x, r, V, Qb)
+            k += 1
+    except Breakdown:
+        res.status = BREAKDOWN
+    res.spmm_count = ctx.spmm
+    if record:
+        res.basis = Qb.Q.copy()
+    return _finish(res, x, rho, rho0, tol, k)
+
+
+# ----------------------------------------------------------------------------------------
+# Communication-avoiding forms: CA-Arnoldi (Algorithm 5) and modified CA-Arnoldi (Alg. 7)
+# ----------------------------------------------------------------------------------------
+
+def _split_blocks(V, AV, t):
+    return [(V[:, i:i + t], AV[:, i:i + t]) for i in range(0, V.shape[1], t)]
+
+
+def ca_enlarged_cg(A, b, part, t, s, tol=1e-8, maxit=1000, x0=None, orth="acholqr",
+                   variant="sre", arnoldi="alg7", breakdown_tol=1e-14, explicit_AW=False,
+                   record=False) -> Result:
+    """CA SRE-CG / CA SRE-CG2 / CA MSDO-CG: Algorithms 4 / 3 / 6 with the basis built by
+    the CA-Arnoldi A-orthonormalisation (Algorithm 5, arnoldi='alg5') or the modified
+    CA-Arnoldi (Algorithm 7, arnoldi='alg7').
+
+    Algorithm 5: W_j = W_{j-1} (k = 1) or A W_{j-1} (k > 1); W_{j+i} = A W_{j+i-1} for
+    i = 1..s-1; V = [W_j .. W_{j+s-1}] is A-orthonormalised against Q (k > 1), then itself.
+    Algorithm 7: as Alg. 5, but W_j is first A-orthonormalised against Q (k > 1) and against
+    itself before the powers are formed.
+    Input block W_{j-1}: T(r_0) at k = 1, else the last t vectors of the previous V
+    (SRE variants); T(r_{k-1}) at every k for MSDO, where W_j = W_{j-1} replaces
+    W_j = A W_{j-1} (Section 3.2).
+    Q: the last (s+1)t vectors (CA SRE-CG) or all previous vectors (CA SRE-CG2, CA MSDO-CG).
+    """
+    if variant not in VARIANTS or arnoldi not in ("alg5", "alg7"):
+        raise ValueError((variant, arnoldi))
+    ctx = _Ctx(A, part, t, orth, breakdown_tol, explicit_AW, record)
+    x, r, rho0 = _start(A, b, x0)
+    res = Result(x=x, iters=0, hist=[rho0], status=OK)
+    _record(ctx, res, x, r)
+    r0 = r.copy()
+    window = []          # CA SRE-CG: t-wide column blocks of the last V's
+    full = _Basis(b.shape[0])   # CA SRE-CG2 / CA MSDO-CG: all previous vectors
+    last = None          # (W_{j-1}, A W_{j-1}) carried from the previous iteration
+    rho, k = rho0, 1
+    kmax = maxit + 1
+    try:
+        while rho > tol * rho0 and k < kmax:
+            Qb = window[-(s + 1):] if variant == "sre" else full
+            # first block W_j
+            if variant == "msdo":
+                Wj = split_T(r, ctx.part, t)
+                AWj = ctx.matmul(Wj)
+            elif k == 1:
+                Wj = split_T(r0, ctx.part, t)
+                AWj = ctx.matmul(Wj)
+            else:
+                Wj = last[1]                               # W_j = A W_{j-1}
+                AWj = ctx.matmul(Wj)
+            if arnoldi == "alg7":
+                if k > 1:
+                    Wj, AWj = ctx.against(Wj, AWj, Qb)
+                Wj, AWj = ctx.self_orth(Wj, AWj)
+            Vb = [(Wj, AWj)]
+            for i in range(1, s):
+                W = Vb[-1][1]                              # W_{j+i} = A W_{j+i-1}
+                Vb.append((W, ctx.matmul(W)))
+            V = np.hstack([v[0] for v in Vb])
+            AV = np.hstack([v[1] for v in Vb])
+            if k > 1:
+                V, AV = ctx.against(V, AV, Qb)
+            V, AV = ctx.self_orth(V, AV)
+            newb = _split_blocks(V, AV, t)
+            if variant == "sre":
+                window = (window + newb)[-(2 * s + 1):]
+            else:
+                full.append(V, AV)
+            last = newb[-1]
+            x, r, rho = _update(ctx, res, x, r, V, AV)
+            res.hist.append(rho)
+            _record(ctx, res, x, r, V, full if variant != "sre" else newb)
+            k += 1
+    except Breakdown:
+        res.status = BREAKDOWN
+    res.spmm_count = ctx.spmm
+    if record and variant != "sre":
+        res.basis = full.Q.copy()
+    return _finish(res, x, rho, rho0, tol, k)
+
+
+# ----------------------------------------------------------------------------------------
+# Restructured SRE-CG (Algorithm 2) and SRE-CG2 (Algorithm 1)
+# ----------------------------------------------------------------------------------------
+
+def restructured_sre_cg(A, b, part, t, s, tol=1e-8, maxit=1000, x0=None, orth="acholqr",
+                        full_history=False, breakdown_tol=1e-14, record=False) -> Result:
+    """Restructured SRE-CG (Algorithm 2; Algorithm 1 with full_history=True): build the s
+    blocks as in Alg. 4 / Alg. 3, then s sequential updates alpha = W_i^T r_{i-1},
+    x_i = x_{i-1} + W_i alpha, r_i = r_{i-1} - A W_i alpha.  The residual norm is checked
+    once every s updates; `iters` counts those outer steps (k_s of Tables 2-3).  With
+    record=True, `xs` holds every inner iterate x_0, x_1, x_2, ... (for s = 1 this is
+    SRE-CG / SRE-CG2 itself)."""
+    ctx = _Ctx(A, part, t, orth, breakdown_tol, False, record)
+    x, r, rho0 = _start(A, b, x0)
+    res = Result(x=x, iters=0, hist=[rho0], status=OK)
+    if record:
+        res.xs.append(x.copy())
+    r0 = r.copy()
+    window = []
+    full = _Basis(b.shape[0])
+    last = None
+    rho, k = rho0, 1
+    kmax = maxit + 1
+    try:
+        while rho > tol * rho0 and k < kmax:
+            Vb = []
+            for i in range(s):
+                if k == 1 and i == 0:
+                    W = split_T(r0, ctx.part, t)
+                    AW = ctx.matmul(W)
+                else:
+                    W = last[1]                            # W_j = A W_{j-1}
+                    AW = ctx.matmul(W)
+                    W, AW = ctx.against(W, AW, full if full_history else window)
+                W, AW = ctx.self_orth(W, AW)
+                last = (W, AW)
+                Vb.append(last)
+                if full_history:
+                    full.append(W, AW)
+                else:
+                    window = (window + [last])[-2:]
+            for (W, AW) in Vb:
+                alpha = W.T @ r
+                x = x + W @ alpha
+                r = r - AW @ alpha
+                if record:
+                    res.xs.append(x.copy())
+            rho = float(np.linalg.norm(r))
+            res.hist.append(rho)
+            k += 1
+    except Breakdown:
+        res.status = BREAKDOWN
+    res.spmm_count = ctx.spmm
+    return _finish(res, x, rho, rho0, tol, k)
+
+
+# ----------------------------------------------------------------------------------------
+# Dispatcher
+# ----------------------------------------------------------------------------------------
+
+def solve(A, b, part, t, s, tol=1e-8, maxit=1000, x0=None, variant="sre", basis="sstep",
+          orth="acholqr", breakdown_tol=1e-14, explicit_AW=False, record=False) -> Result:
+    """Select the algorithm: basis 'sstep' -> Alg. 4 (sre) / Alg. 3 (sre2) / Alg. 6 (msdo);
+    basis 'ca5' / 'ca7' -> the CA form of the variant with Alg. 5 / Alg. 7."""
+    if basis == "sstep":
+        if variant == "msdo":
+            return sstep_msdo_cg(A, b, part, t, s, tol, maxit, x0, orth, breakdown_tol,
+                                 explicit_AW, record)
+        return sstep_sre_cg(A, b, part, t, s, tol, maxit, x0, orth, variant == "sre2",
+                            breakdown_tol, explicit_AW, record)
+    return ca_enlarged_cg(A, b, part, t, s, tol, maxit, x0, orth, variant,
+                          "alg5" if basis == "ca5" else "alg7", breakdown_tol, explicit_AW,
+                          record)
