@@ -19,14 +19,20 @@ the permutation the GPU library must reproduce.
 Readings where the paper is silent or refers to the author's thesis (all listed in
 the design doc too):
   * CGS2 against Q (thesis Alg. 18, not printed): two passes of C = Q^T (A W),
-    W <- W - Q C, with A W carried along: AW <- AW - (AQ) C.
+    W <- W - Q C.  The A-inner products use a fresh sparse product A W of the current W in
+    each pass (and one more after the second pass for the Gram matrix below).
   * A-CholQR (thesis Alg. 21): G = W^T (A W) = R^T R (upper Cholesky of the upper
-    triangle of G), W <- W R^{-1}, AW <- AW R^{-1}.
+    triangle of G), W <- W R^{-1}; the product A W is carried through the triangular
+    factor, A W <- (A W) R^{-1}, and serves as the next candidate block A W_j and as the
+    block A V of the residual update.
   * Pre-CholQR (thesis Alg. 23): thin Euclidean QR W = Z S with diag(S) > 0 first, then
-    A-CholQR of Z (AZ = AW S^{-1}).
-  * A W is carried by the same linear recurrences as W, so each new block costs exactly one
-    sparse product; the next candidate block A W_{j-1} is the carried A W_{j-1}.
-    `explicit_AW=True` recomputes A W with a sparse product after every step instead.
+    A-CholQR of Z (A Z = (A W) S^{-1}, again carried only through a triangular factor).
+  * Why fresh products: carrying A W through the CGS updates as well (A W <- A W - (A Q) C)
+    lets the error of A Q grow by the size of C at every block; on the skyscraper problem
+    the A-orthogonality of s-step SRE-CG2 then decays to O(1) and the Gram matrix turns
+    indefinite, whereas Section 4 reports s-step SRE-CG2 converging in k_s iterations on
+    every test matrix.  `carried_cgs=True` keeps that carried form for comparison;
+    `explicit_AW=True` also recomputes A W after the triangular factor.
   * Missing window blocks in the first iterations (W_{j-2} for j < 3) are skipped.
   * Stopping rule: while rho > tol*rho0 and iterations < maxit, rho = ||r_k||_2 of the
     recursively updated residual, checked once per s-step iteration.
@@ -137,9 +143,20 @@ def pre_cholqr(W, AW, breakdown_tol):
     return a_cholqr(Z, right_solve_upper(AW, S), breakdown_tol)
 
 
-def cgs2_against(W, AW, Q, AQ):
+def cgs2_against(W, AW, Q, matmul):
     """CGS2 A-orthonormalisation of W against the A-orthonormal Q: two passes of
-    C = Q^T (A W), W <- W - Q C, A W <- A W - (A Q) C."""
+    C = Q^T (A W), W <- W - Q C, where A W is a fresh sparse product of the current W
+    (`AW` holds A W on entry; `matmul(X)` returns A X).  Returns W and A W."""
+    for _ in range(2):
+        C = Q.T @ AW
+        W = W - Q @ C
+        AW = matmul(W)
+    return W, AW
+
+
+def cgs2_against_carried(W, AW, Q, AQ):
+    """CGS2 with A W carried by the same recurrence, A W <- A W - (A Q) C (the form whose
+    A-orthogonality decays; kept for comparison only)."""
     for _ in range(2):
         C = Q.T @ AW
         W = W - Q @ C
@@ -154,13 +171,14 @@ def cgs2_against(W, AW, Q, AQ):
 class _Ctx:
     """Per-solve state: the operator, options and bookkeeping."""
 
-    def __init__(self, A, part, t, orth, breakdown_tol, explicit_AW, record):
+    def __init__(self, A, part, t, orth, breakdown_tol, explicit_AW, record, carried_cgs=False):
         self.A = A.to_scipy() if hasattr(A, "to_scipy") else sp.csr_matrix(A)
         self.part = np.asarray(part)
         self.t = t
         self.orth = orth
         self.tol_bd = breakdown_tol
         self.explicit = explicit_AW
+        self.carried = carried_cgs
         self.record = record
         self.spmm = 0
 
@@ -189,10 +207,9 @@ class _Ctx:
                 return W, AW
             Q = np.hstack([b[0] for b in blocks])
             AQ = np.hstack([b[1] for b in blocks])
-        W, AW = cgs2_against(W, AW, Q, AQ)
-        if self.explicit:
-            AW = self.A @ W
-        return W, AW
+        if self.carried:
+            return cgs2_against_carried(W, AW, Q, AQ)
+        return cgs2_against(W, AW, Q, self.matmul)
 
 
 class _Basis:
@@ -319,7 +336,7 @@ def cg(A, b, x0=None, tol=1e-8, maxit=10000, record=False) -> Result:
 
 def sstep_sre_cg(A, b, part, t, s, tol=1e-8, maxit=1000, x0=None, orth="acholqr",
                  full_history=False, breakdown_tol=1e-14, explicit_AW=False,
-                 record=False) -> Result:
+                 record=False, carried_cgs=False) -> Result:
     """s-step SRE-CG (Algorithm 4); with full_history=True, s-step SRE-CG2 (Algorithm 3).
 
     Iteration k builds s blocks W_j..W_{j+s-1}, j = (k-1)s+1.  W_1 = T(r_0) is only
@@ -327,7 +344,7 @@ def sstep_sre_cg(A, b, part, t, s, tol=1e-8, maxit=1000, x0=None, orth="acholqr"
     against W_{j-2}, W_{j-1} (Alg. 4) or against all previous blocks (Alg. 3), then against
     itself.  Then alpha = V^T r_{k-1}, x_k = x_{k-1} + V alpha, r_k = r_{k-1} - A V alpha.
     """
-    ctx = _Ctx(A, part, t, orth, breakdown_tol, explicit_AW, record)
+    ctx = _Ctx(A, part, t, orth, breakdown_tol, explicit_AW, record, carried_cgs)
     x, r, rho0 = _start(A, b, x0)
     res = Result(x=x, iters=0, hist=[rho0], status=OK)
     _record(ctx, res, x, r)
@@ -380,11 +397,12 @@ def sstep_sre_cg2(*args, **kw) -> Result:
 # ----------------------------------------------------------------------------------------
 
 def sstep_msdo_cg(A, b, part, t, s, tol=1e-8, maxit=1000, x0=None, orth="acholqr",
-                  breakdown_tol=1e-14, explicit_AW=False, record=False) -> Result:
+                  breakdown_tol=1e-14, explicit_AW=False, record=False,
+                  carried_cgs=False) -> Result:
     """s-step MSDO-CG (Algorithm 6).  Iteration k: W_1 = T(r_{k-1}) A-orthonormalised
     against Q (k > 1) and itself; W_{i+1} = A W_i against Q and itself, i = 1..s-1; every
     block joins V and Q.  Then alpha = V^T r_{k-1} and the x / r updates."""
-    ctx = _Ctx(A, part, t, orth, breakdown_tol, explicit_AW, record)
+    ctx = _Ctx(A, part, t, orth, breakdown_tol, explicit_AW, record, carried_cgs)
     x, r, rho0 = _start(A, b, x0)
     res = Result(x=x, iters=0, hist=[rho0], status=OK)
     _record(ctx, res, x, r)
@@ -431,7 +449,7 @@ def _split_blocks(V, AV, t):
 
 def ca_enlarged_cg(A, b, part, t, s, tol=1e-8, maxit=1000, x0=None, orth="acholqr",
                    variant="sre", arnoldi="alg7", breakdown_tol=1e-14, explicit_AW=False,
-                   record=False) -> Result:
+                   record=False, carried_cgs=False) -> Result:
     """CA SRE-CG / CA SRE-CG2 / CA MSDO-CG: Algorithms 4 / 3 / 6 with the basis built by
     the CA-Arnoldi A-orthonormalisation (Algorithm 5, arnoldi='alg5') or the modified
     CA-Arnoldi (Algorithm 7, arnoldi='alg7').
@@ -447,7 +465,7 @@ def ca_enlarged_cg(A, b, part, t, s, tol=1e-8, maxit=1000, x0=None, orth="acholq
     """
     if variant not in VARIANTS or arnoldi not in ("alg5", "alg7"):
         raise ValueError((variant, arnoldi))
-    ctx = _Ctx(A, part, t, orth, breakdown_tol, explicit_AW, record)
+    ctx = _Ctx(A, part, t, orth, breakdown_tol, explicit_AW, record, carried_cgs)
     x, r, rho0 = _start(A, b, x0)
     res = Result(x=x, iters=0, hist=[rho0], status=OK)
     _record(ctx, res, x, r)
@@ -506,14 +524,15 @@ def ca_enlarged_cg(A, b, part, t, s, tol=1e-8, maxit=1000, x0=None, orth="acholq
 # ----------------------------------------------------------------------------------------
 
 def restructured_sre_cg(A, b, part, t, s, tol=1e-8, maxit=1000, x0=None, orth="acholqr",
-                        full_history=False, breakdown_tol=1e-14, record=False) -> Result:
+                        full_history=False, breakdown_tol=1e-14, record=False,
+                        carried_cgs=False) -> Result:
     """Restructured SRE-CG (Algorithm 2; Algorithm 1 with full_history=True): build the s
     blocks as in Alg. 4 / Alg. 3, then s sequential updates alpha = W_i^T r_{i-1},
     x_i = x_{i-1} + W_i alpha, r_i = r_{i-1} - A W_i alpha.  The residual norm is checked
     once every s updates; `iters` counts those outer steps (k_s of Tables 2-3).  With
     record=True, `xs` holds every inner iterate x_0, x_1, x_2, ... (for s = 1 this is
     SRE-CG / SRE-CG2 itself)."""
-    ctx = _Ctx(A, part, t, orth, breakdown_tol, False, record)
+    ctx = _Ctx(A, part, t, orth, breakdown_tol, False, record, carried_cgs)
     x, r, rho0 = _start(A, b, x0)
     res = Result(x=x, iters=0, hist=[rho0], status=OK)
     if record:
@@ -562,15 +581,56 @@ def restructured_sre_cg(A, b, part, t, s, tol=1e-8, maxit=1000, x0=None, orth="a
 # ----------------------------------------------------------------------------------------
 
 def solve(A, b, part, t, s, tol=1e-8, maxit=1000, x0=None, variant="sre", basis="sstep",
-          orth="acholqr", breakdown_tol=1e-14, explicit_AW=False, record=False) -> Result:
+          orth="acholqr", breakdown_tol=1e-14, explicit_AW=False, record=False,
+          carried_cgs=False) -> Result:
     """Select the algorithm: basis 'sstep' -> Alg. 4 (sre) / Alg. 3 (sre2) / Alg. 6 (msdo);
     basis 'ca5' / 'ca7' -> the CA form of the variant with Alg. 5 / Alg. 7."""
     if basis == "sstep":
         if variant == "msdo":
             return sstep_msdo_cg(A, b, part, t, s, tol, maxit, x0, orth, breakdown_tol,
-                                 explicit_AW, record)
+                                 explicit_AW, record, carried_cgs)
         return sstep_sre_cg(A, b, part, t, s, tol, maxit, x0, orth, variant == "sre2",
-                            breakdown_tol, explicit_AW, record)
+                            breakdown_tol, explicit_AW, record, carried_cgs)
     return ca_enlarged_cg(A, b, part, t, s, tol, maxit, x0, orth, variant,
                           "alg5" if basis == "ca5" else "alg7", breakdown_tol, explicit_AW,
-                          record)
+                          record, carried_cgs)
+
+
+# ----------------------------------------------------------------------------------------
+# Adjoint gradients of a solve (differentiable configuration; not in the paper)
+# ----------------------------------------------------------------------------------------
+
+def grad_A_values(A, lam, x):
+    """dL/dA_ij = -lambda_i x_j for every stored nonzero (i, j) of A (CSR order), where
+    x = A^{-1} b and lambda = A^{-1} dL/dx (A symmetric)."""
+    out = np.empty(A.nnz)
+    for i in range(A.n):
+        for k in range(A.rowptr[i], A.rowptr[i + 1]):
+            out[k] = -lam[i] * x[A.colind[k]]
+    return out
+
+
+def diffusion2d_grad_logkappa(log_kappa, nx, ny, lam, x, ax=1.0, ay=1.0):
+    """dL/dlog(kappa) for the 2D edge-form diffusion matrix
+    A = sum_e w_e (e_p - e_q)(e_p - e_q)^T + sum_faces a kappa_p e_p e_p^T,
+    w_e = a * 2 k_p k_q / (k_p + k_q): loop over edges and Dirichlet faces,
+    dL/dw = -lambda^T (dA/dw) x, chained through dw/dk and dk/dlog k = k."""
+    k = np.exp(np.asarray(log_kappa, dtype=np.float64).reshape(ny, nx))
+    g = np.zeros((ny, nx))
+    lam = np.asarray(lam).reshape(ny, nx)
+    x = np.asarray(x).reshape(ny, nx)
+    for j in range(ny):
+        for i in range(nx):
+            for (di, dj, a) in ((1, 0, ax), (0, 1, ay)):
+                i2, j2 = i + di, j + dj
+                if i2 < nx and j2 < ny:
+                    kp, kq = k[j, i], k[j2, i2]
+                    dLdw = -(lam[j, i] - lam[j2, i2]) * (x[j, i] - x[j2, i2])
+                    g[j, i] += dLdw * a * 2.0 * kq * kq / (kp + kq) ** 2
+                    g[j2, i2] += dLdw * a * 2.0 * kp * kp / (kp + kq) ** 2
+            # Dirichlet faces: two per axis at the ends of the grid
+            faces = (i == 0) + (i == nx - 1)
+            g[j, i] += faces * ax * (-lam[j, i] * x[j, i])
+            faces = (j == 0) + (j == ny - 1)
+            g[j, i] += faces * ay * (-lam[j, i] * x[j, i])
+    return (g * k).ravel()
