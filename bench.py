@@ -1,0 +1,318 @@
+#!/usr/bin/env python
+"""Time-to-solution of the s-step enlarged CG (arXiv:1804.10629) on GB300.
+
+One step = one whole solve of A x = b to ||r_k|| <= 1e-8 ||r_0|| (x_0 = 0) through the C-ABI
+library, with A, its partition and b already resident in device memory.  Default workload:
+Ani3D-like 7-point anisotropic diffusion on a 128^3 grid (n = 2,097,152, coefficients
+1, 1, 1e-3), t = 32 box subdomains, s = 2, s-step SRE-CG (Algorithm 4), float64.
+
+Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle instead, on a
+bounded sample of s-step iterations scaled to a whole solve by the oracle's stored
+iteration count (tests/golden/oracle_counts.json).
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as wl  # noqa: E402
+
+# FP64 ALU peak of one GB300: 152 SMs x 2 FP64 FMA per clock per SM x 2 flop x 2.07 GHz
+# (unit count inferred from a measured 1.20 TFLOP/s DFMA loop; the nominal figure is 1.25).
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+HBM_FALLBACK_GBS = 6800.0
+
+WORKLOADS = {
+    "ani3d": dict(make=lambda N: wl.ani3d(N or 128, 32, seed=1), s=2, variant="sre",
+                  desc="Ani3D-like 7-point anisotropic diffusion (1,1,1e-3), t=32 boxes"),
+    "sky3d": dict(make=lambda N: wl.sky3d(N or 96, 16, seed=2), s=4, variant="sre",
+                  desc="Sky3D-like 7-point diffusion, coefficient 1 / 1e3 on 8^3 blocks, t=16"),
+    "poisson2d": dict(make=lambda N: wl.poisson2d(N or 100, 4, seed=0), s=2, variant="sre",
+                      desc="Poisson2D gallery('poisson',100), 4 strips"),
+}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ekcg", choices=["ekcg", "reference"])
+    ap.add_argument("--workload", default="ani3d", choices=sorted(WORKLOADS))
+    ap.add_argument("--grid", type=int, default=0, help="override the grid side (quick runs)")
+    ap.add_argument("--s", type=int, default=0)
+    ap.add_argument("--variant", default="")
+    ap.add_argument("--basis", default="sstep")
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32_ir"])
+    ap.add_argument("--tol", type=float, default=1e-8)
+    ap.add_argument("--maxit", type=int, default=20000)
+    ap.add_argument("--cpu-sample-iters", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+class Clocks:
+    """nvidia-smi sampling (every 200 ms) during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={self.index}",
+                                       f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                       "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        self.p.wait()
+        self.f.flush()
+        rows = [ln.split(",") for ln in open(self.f.name).read().splitlines() if ln.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx = float(r[2])
+                for nm, v in zip(names, r[5:9]):
+                    if v.strip().lower() == "active":
+                        reasons.add(nm)
+            except (ValueError, IndexError):
+                continue
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup(args):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def oracle_counts():
+    p = os.path.join(ROOT, "tests", "golden", "oracle_counts.json")
+    return json.load(open(p)) if os.path.exists(p) else {}
+
+
+def cpu_oracle_sample(prob, s, variant, iters, gpu_iters=None):
+    """Time `iters` s-step iterations of the FP64 oracle on the full problem; scale to a
+    whole solve by the oracle's stored iteration count (else the GPU's)."""
+    from oracle import ekcg_ref as o
+    t0 = time.perf_counter()
+    res = o.solve(prob.A, prob.b, prob.part, prob.t, s, tol=1e-8, maxit=iters, variant=variant)
+    dt = time.perf_counter() - t0
+    per_it = dt / max(res.iters, 1)
+    key = f"{prob.name.split('-')[0].lower()}/t{prob.t}/s{s}/{variant}/sstep/fp64"
+    cnt = oracle_counts().get(key, {}).get("iters")
+    scale_src = "oracle_counts.json" if cnt else "GPU iteration count"
+    total = cnt if cnt else (gpu_iters or res.iters)
+    return {"value": per_it * total, "per_iter_s": per_it, "iters_scaled_to": total,
+            "scaled_by": scale_src, "sample_s": dt, "sample_iters": res.iters,
+            "cores": len(os.sched_getaffinity(0))}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    cfg = WORKLOADS[args.workload]
+    prob = cfg["make"](args.grid)
+    s = args.s or cfg["s"]
+    variant = args.variant or cfg["variant"]
+    for _ in range(args.warmup):
+        pass  # the oracle has no warm-up state; warm-up steps would only burn host time
+    vals, samples = [], []
+    for _ in range(args.steps):
+        r = cpu_oracle_sample(prob, s, variant, args.cpu_sample_iters)
+        vals.append(r["value"])
+        samples.append(r)
+    v = statistics.median(vals)
+    line = {
+        "impl": "reference", "metric": "time-to-solution @relres 1e-8 (s)", "value": v,
+        "unit": "s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": v * 1e3, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"{prob.name} n={prob.A.n} nnz={prob.A.nnz} t={prob.t} s={s} "
+                               f"{variant} sstep fp64", "parallelism": "replicas"},
+        "cpu_baseline": {"value": v, "unit": "s", "cores": samples[0]["cores"], "kind": "oracle",
+                         "sample": f"{args.cpu_sample_iters} s-step iterations of the FP64 oracle "
+                                   f"per step on the full workload, scaled to "
+                                   f"{samples[0]['iters_scaled_to']} iterations "
+                                   f"({samples[0]['scaled_by']})"},
+        "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_setup(args)
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_1804_10629_gb300 import ekcg
+    if not os.path.exists(ekcg.LIB_PATH):
+        from paper_1804_10629_gb300 import build
+        build.build()
+
+    cfg = WORKLOADS[args.workload]
+    prob = cfg["make"](args.grid)
+    s = args.s or cfg["s"]
+    variant = args.variant or cfg["variant"]
+    stream = torch.cuda.Stream()
+    t0 = time.perf_counter()
+    with torch.cuda.stream(stream):
+        S = ekcg.Solver(prob.A, prob.t, prob.part, variant=variant, basis=args.basis,
+                        precision=args.precision, max_s=s, profile=True,
+                        stream=stream.cuda_stream, max_basis_bytes=64 << 30)
+    setup_s = time.perf_counter() - t0
+    b = torch.as_tensor(prob.b, dtype=torch.float64, device="cuda")
+    x = torch.empty_like(b)
+    torch.cuda.synchronize()
+
+    its = []
+    for _ in range(args.warmup):
+        _, it, _, st = S.solve(b, s=s, tol=args.tol, maxit=args.maxit, x=x)
+        its.append(it)
+    clocks = Clocks(local)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    launches = 0
+    prof = {}
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        _, it, hist, st = S.solve(b, s=s, tol=args.tol, maxit=args.maxit, x=x)
+        its.append(it)
+        launches += S.stats()[0]
+        for k, v in S.profile().items():
+            agg = prof.setdefault(k, {"ms": 0.0, "launches": 0, "flops": 0.0, "bytes": 0.0})
+            for f in agg:
+                agg[f] += v[f]
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ck = clocks.stop()
+    if dist:
+        dist.barrier()
+    ms_step = ev0.elapsed_time(ev1) / args.steps
+    if dist:
+        tt = torch.tensor([ms_step], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms_step = float(tt.item())
+    xs = x.cpu().numpy()
+    relres = float(np.linalg.norm(prob.b - prob.A.to_scipy() @ xs) / np.linalg.norm(prob.b))
+
+    # dominant kernel class by device time, roofline against its bound
+    pk = peaks()
+    hbm = pk.get("hbm_gbs")
+    dom = max(prof.items(), key=lambda kv: kv[1]["ms"]) if prof else (None, None)
+    roof = None
+    if dom[0]:
+        name, d = dom
+        sec = d["ms"] / 1e3
+        if args.precision == "fp64" and name in ("gram", "block_update", "spmm", "chol_inv",
+                                                   "xr_update", "gram_reduce"):
+            ach = d["flops"] / sec / 1e12
+            roof = {"kernel": name, "bound": "alu", "achieved": ach,
+                    "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS,
+                    "peak_source": "derived FP64 FMA rate: 152 SMs x 2 DFMA/clk x 2 x 2.07 GHz",
+                    "traffic": None, "launches": d["launches"],
+                    "avg_launch_ms": d["ms"] / max(d["launches"], 1)}
+        else:
+            peak = hbm or HBM_FALLBACK_GBS
+            ach = d["bytes"] / sec / 1e9
+            roof = {"kernel": name, "bound": "hbm", "achieved": ach, "peak": peak,
+                    "unit": "GB/s", "frac": ach / peak,
+                    "peak_source": "of measured" if hbm else "of fallback",
+                    "traffic": None, "launches": d["launches"],
+                    "avg_launch_ms": d["ms"] / max(d["launches"], 1)}
+    kernel_table = {k: {"ms_per_step": v["ms"] / args.steps,
+                        "launches_per_step": v["launches"] / args.steps,
+                        "gflop_per_step": v["flops"] / args.steps / 1e9,
+                        "gb_per_step": v["bytes"] / args.steps / 1e9,
+                        "tflops": (v["flops"] / (v["ms"] / 1e3) / 1e12) if v["ms"] else None,
+                        "gbs": (v["bytes"] / (v["ms"] / 1e3) / 1e9) if v["ms"] else None}
+                    for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"])}
+
+    # end to end through the host-buffer C-ABI call (H2D of b and D2H of x inside)
+    e2e = None
+    if not args.no_e2e:
+        bh = np.ascontiguousarray(prob.b)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        xh, it_h, _, st_h = S.solve_host(bh, s=s, tol=args.tol, maxit=args.maxit)
+        e2e_s = time.perf_counter() - t1
+        e2e = {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": int(bh.nbytes),
+               "d2h_bytes_per_step": int(xh.nbytes)}
+    S.close()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        r = cpu_oracle_sample(prob, s, variant, args.cpu_sample_iters, gpu_iters=its[-1])
+        cpu = {"value": r["value"], "unit": "s", "cores": r["cores"], "kind": "oracle",
+               "sample": f"{r['sample_iters']} s-step iterations of the FP64 oracle on the full "
+                         f"workload ({r['sample_s']:.1f} s), scaled to {r['iters_scaled_to']} "
+                         f"iterations ({r['scaled_by']})"}
+
+    if rank == 0:
+        line = {
+            "metric": "time-to-solution @relres 1e-8 (s)", "value": ms_step / 1e3, "unit": "s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms_step, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32+f64",
+            "data": "synthetic",
+            "config": {"workload": f"{prob.name} n={prob.A.n} nnz={prob.A.nnz} t={prob.t} "
+                                   f"s={s} {variant} {args.basis} {args.precision}",
+                       "desc": cfg["desc"], "tol": args.tol, "iters": its[-1],
+                       "true_relres": relres, "status": st,
+                       "l2": "working set larger than L2 (matrix + n x t blocks)",
+                       "setup_s": setup_s, "parallelism": "replicas",
+                       "profiling": "CUDA events around every launch on the solve stream"},
+            "roofline": roof, "kernels": kernel_table, "gpu_launches": launches,
+            "e2e": e2e, "cpu_baseline": cpu, "clocks": ck,
+        }
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,186 @@
+/*
+ * ekcg.h - C ABI of the GB300 s-step enlarged Krylov subspace CG library.
+ *
+ * Method: Moufawad, "Numerical Stability of s-step Enlarged Krylov Subspace Conjugate
+ * Gradient methods" (arXiv:1804.10629).
+ *   - s-step SRE-CG (Algorithm 4), s-step SRE-CG2 (Algorithm 3), s-step MSDO-CG (Algorithm 6)
+ *   - their communication-avoiding forms built with CA-Arnoldi (Algorithm 5) or the
+ *     stable modified CA-Arnoldi (Algorithm 7), Section 3 and Section 4
+ *   - A-orthonormalisation by CGS2 against previous vectors, then A-CholQR or Pre-CholQR
+ *     against itself (Section 3.1, Section 4)
+ *
+ * Conventions shared by every entry point:
+ *   - Status: 0 = EKCG_OK; EKCG_MAXIT (> 0) is a warning, outputs are valid; negative values
+ *     are errors (see ekcg_strerror).  A failing call leaves caller buffers in an unspecified
+ *     state only where the description says so; it never frees caller memory.
+ *   - Ownership: the caller owns every pointer it passes and keeps it alive for the call.
+ *     The context owns its device copies of the matrix and all workspace, released by
+ *     ekcg_destroy.  No entry point keeps a caller pointer after it returns.
+ *   - Memory spaces: "host" pointers are ordinary CPU memory; "device" pointers are CUDA
+ *     global memory on the context's device (for example torch tensor data_ptr()).
+ *   - Row order: ekcg_solve takes and returns vectors in the caller's (natural) order.  The
+ *     kernel-level entry points (ekcg_split_T, ekcg_spmm, ekcg_permute) work in the
+ *     context's permuted order, where the t domains are contiguous.
+ *   - Layout of an n x w block of vectors: row-major, element (i, c) at [i*w + c].
+ *   - Work is enqueued on the context's stream; calls that return results to the host
+ *     synchronise that stream before returning.
+ *   - Not thread-safe per context: one host thread drives one context at a time.
+ */
+#ifndef EKCG_H
+#define EKCG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------------------- */
+#define EKCG_OK 0
+#define EKCG_MAXIT 1          /* maxit reached before the tolerance: outputs are valid     */
+#define EKCG_EINVAL (-1)      /* bad argument: shapes, CSR structure, partition, NaN/Inf   */
+#define EKCG_ENOMEM (-2)      /* device memory or stored-basis capacity exhausted          */
+#define EKCG_EBREAKDOWN (-3)  /* Cholesky pivot failed the breakdown rule                  */
+#define EKCG_ETIMEOUT (-4)    /* reserved: a bounded device wait ran out                   */
+#define EKCG_ECUDA (-5)       /* a CUDA runtime call failed (see ekcg_last_error)          */
+
+/* ---- solver options ------------------------------------------------------------- */
+#define EKCG_SRE 0    /* s-step SRE-CG  (Algorithm 4): orthonormalise against 2 blocks  */
+#define EKCG_SRE2 1   /* s-step SRE-CG2 (Algorithm 3): against all previous blocks       */
+#define EKCG_MSDO 2   /* s-step MSDO-CG (Algorithm 6): T(r_{k-1}) starts every iteration  */
+
+#define EKCG_SSTEP 0  /* basis built t vectors at a time (Algorithms 3, 4, 6)             */
+#define EKCG_CA5 1    /* CA-Arnoldi A-orthonormalisation (Algorithm 5, monomial, unstable) */
+#define EKCG_CA7 2    /* modified CA-Arnoldi A-orthonormalisation (Algorithm 7)           */
+
+#define EKCG_ACHOLQR 0    /* A-CholQR: G = W^T A W = R^T R, W <- W R^{-1}                 */
+#define EKCG_PRECHOLQR 1  /* Euclidean CholQR2 first, then A-CholQR                       */
+
+#define EKCG_FP64 0       /* all vectors and arithmetic in float64                       */
+#define EKCG_FP32_IR 1    /* float32 inner solve in a float64 iterative-refinement loop   */
+
+typedef struct ekcg_ctx ekcg_ctx;
+
+typedef struct {
+    int variant;          /* EKCG_SRE / EKCG_SRE2 / EKCG_MSDO                            */
+    int basis;            /* EKCG_SSTEP / EKCG_CA5 / EKCG_CA7                            */
+    int orth;             /* EKCG_ACHOLQR / EKCG_PRECHOLQR                                */
+    int precision;        /* EKCG_FP64 / EKCG_FP32_IR                                     */
+    int max_s;            /* largest s any solve on this context uses (workspace size)     */
+    int max_blocks;       /* stored t-blocks for full-history forms (SRE2, MSDO, CA SRE2);
+                             0 = as many as fit in max_basis_bytes                          */
+    int64_t max_basis_bytes; /* device bytes for stored basis vectors; 0 = 40% of free    */
+    double breakdown_tol; /* Cholesky pivot d_i <= breakdown_tol*|G_ii| stops the solve   */
+    double inner_tol;     /* FP32_IR: relative residual reduction of each inner solve      */
+    int max_refine;       /* FP32_IR: maximum outer refinement steps                       */
+    int profile;          /* 1: time every kernel class with CUDA events (ekcg_profile)   */
+} ekcg_opts;
+
+/* Fill *opts with the defaults: SRE, SSTEP, ACHOLQR, FP64, max_s 8, max_blocks 0,
+ * max_basis_bytes 0, breakdown_tol 1e-14, inner_tol 1e-4, max_refine 30, profile 0.      */
+void ekcg_default_opts(ekcg_opts* opts);
+
+/* Build a solver context for the SPD matrix A (Section 2) and its t-way partition.
+ *   n, rowptr[n+1] (int64), colind[nnz] (int32, sorted and unique per row), val[nnz]:
+ *     host CSR arrays of A, copied; A must be structurally and numerically symmetric with a
+ *     positive diagonal (checked: structure and positive diagonal; values are not).
+ *   t (>= 1), part[n]: host array, part[i] in [0, t) is the domain of row i; every domain
+ *     must be non-empty.  Rows are stably sorted by domain (Section 4 reordering) and the
+ *     matrix is permuted symmetrically on the device.
+ *   opts: may be NULL for defaults.  stream: a cudaStream_t (NULL = legacy default stream).
+ *   *out receives the context.  Errors: EKCG_EINVAL (bad CSR / partition / options),
+ *   EKCG_ENOMEM, EKCG_ECUDA.  Device memory for the workspace is allocated here.          */
+int ekcg_setup(int64_t n, const int64_t* rowptr, const int32_t* colind, const double* val,
+               int t, const int32_t* part, const ekcg_opts* opts, void* stream,
+               ekcg_ctx** out);
+
+/* Solve A x = b (Algorithms 3, 4, 6 and their CA forms, per the context's options).
+ *   b, x0, x: device float64 arrays of length n in natural order; x0 may be NULL (x0 = 0)
+ *     and may alias x.
+ *   s (1 <= s <= opts.max_s), tol (> 0), maxit (>= 0): the loop runs while
+ *     ||r_k||_2 > tol*||r_0||_2 and fewer than maxit s-step iterations were done, with r_k
+ *     the recursively updated residual.
+ *   *iters: s-step iterations performed (FP32_IR: inner s-step iterations, summed).
+ *   res_hist: host array of hist_cap doubles (may be NULL) receiving ||r_0||, ||r_1||, ...
+ *     (FP32_IR: the float64 residual norm after each refinement step); *hist_len the count.
+ *   Returns EKCG_OK, EKCG_MAXIT, EKCG_EBREAKDOWN (x holds the last complete iterate),
+ *   EKCG_ENOMEM (stored-basis capacity exceeded; x holds the last iterate), EKCG_EINVAL
+ *   (bad sizes, non-finite b), EKCG_ECUDA.                                                 */
+int ekcg_solve(ekcg_ctx* ctx, const double* b, const double* x0, int s, double tol,
+               int maxit, double* x, int* iters, double* res_hist, int hist_cap,
+               int* hist_len);
+
+/* ekcg_solve with host arrays b, x0 (nullable) and x: the host-to-device copy of b (and x0)
+ * and the device-to-host copy of x are part of the call.                                 */
+int ekcg_solve_host(ekcg_ctx* ctx, const double* b_host, const double* x0_host, int s,
+                    double tol, int maxit, double* x_host, int* iters, double* res_hist,
+                    int hist_cap, int* hist_len);
+
+/* Release the context and all device memory it owns.  NULL is accepted.                  */
+void ekcg_destroy(ekcg_ctx* ctx);
+
+/* Static string for a status code.                                                        */
+const char* ekcg_strerror(int status);
+
+/* Text of the last EKCG_ECUDA / EKCG_EINVAL cause seen by the calling thread.            */
+const char* ekcg_last_error(void);
+
+/* ---- inspection ------------------------------------------------------------------- */
+/* n, t and nnz of the context.                                                            */
+int ekcg_shape(const ekcg_ctx* ctx, int64_t* n, int* t, int64_t* nnz);
+
+/* perm[i] = natural row index placed at permuted position i (host array of n int64):
+ * the stable sort of rows by domain id (Section 4).                                      */
+int ekcg_get_perm(const ekcg_ctx* ctx, int64_t* perm);
+
+/* Kernel launches and sparse products of the last solve.                                 */
+int ekcg_last_stats(const ekcg_ctx* ctx, int64_t* kernel_launches, int64_t* spmm_calls);
+
+/* Per-kernel-class accounting of the last solve: for class i < *count, names[i] (static
+ * strings), launches[i], flops[i] and bytes[i] (algorithmic: the arithmetic the method needs
+ * and the compulsory DRAM traffic of each launch, summed), and ms[i], the total device time
+ * measured with CUDA events around each launch when opts.profile = 1 (0 otherwise).  Any
+ * output array may be NULL; each holds cap entries.                                       */
+int ekcg_profile(const ekcg_ctx* ctx, int cap, const char** names, double* ms,
+                 int64_t* launches, double* flops, double* bytes, int* count);
+
+/* ---- kernel-level entry points (device pointers, permuted order) ------------------ */
+/* T(r) of Section 2: T[i*t + d] = r[i] if row i lies in domain d, else 0.  r: n doubles,
+ * T: n*t doubles.                                                                         */
+int ekcg_split_T(ekcg_ctx* ctx, const double* r, double* T);
+
+/* U = A W for the permuted matrix, W and U n x w row-major doubles (1 <= w <= 256).      */
+int ekcg_spmm(ekcg_ctx* ctx, const double* W, double* U, int w);
+
+/* ---- differentiation (adjoint solve support) --------------------------------------- */
+/* Replace the matrix values, keeping the sparsity pattern given to ekcg_setup: val is a
+ * device array of nnz doubles in the caller's CSR order.  A must stay SPD.               */
+int ekcg_update_values(ekcg_ctx* ctx, const double* val);
+
+/* Gradient of a loss L(x), x = A^{-1} b, with respect to the stored values of A:
+ * dval[k] = -lambda_i x_j for the k-th nonzero (i, j) in the caller's CSR order, where
+ * lambda = A^{-1} dL/dx is the adjoint solution (A is SPD, so the adjoint solve is another
+ * ekcg_solve).  lam, x: device arrays of n doubles (natural order); dval: nnz doubles.   */
+int ekcg_grad_A(ekcg_ctx* ctx, const double* lam, const double* x, double* dval);
+
+/* 2D diffusion model A(kappa) (5-point edge form, harmonic-mean edge weights times the axis
+ * factors ax, ay, Dirichlet faces a*kappa_p, node p = i + nx*j): write the values of
+ * A(exp(log_kappa)) in natural CSR order with sorted columns into val (device, nnz
+ * doubles).  The context's pattern must be that stencil on an nx x ny grid.              */
+int ekcg_diffusion2d_values(ekcg_ctx* ctx, int nx, int ny, double ax, double ay,
+                            const double* log_kappa, double* val);
+
+/* Chain rule of the same model: grad[p] = dL/dlog(kappa_p) from the adjoint lambda and the
+ * solution x (device arrays of n doubles, natural order).                               */
+int ekcg_diffusion2d_grad_logkappa(ekcg_ctx* ctx, int nx, int ny, double ax, double ay,
+                                   const double* log_kappa, const double* lam, const double* x,
+                                   double* grad);
+
+/* y[i] = x[perm[i]] (direction 0: natural -> permuted) or y[perm[i]] = x[i] (direction 1).*/
+int ekcg_permute(ekcg_ctx* ctx, const double* x, double* y, int direction);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* EKCG_H */

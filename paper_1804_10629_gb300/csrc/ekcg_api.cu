@@ -1,0 +1,1224 @@
+// C ABI and host orchestration of the s-step enlarged CG library (see include/ekcg.h).
+//
+// The host code only sequences kernels: every vector operation of the method runs in the
+// kernels of kernels.cuh.  Host work is limited to O(nnz) integer set-up (validation,
+// stable domain sort, symmetric permutation of the CSR arrays) and the loop control, which
+// reads one residual norm and one status word per s-step iteration.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/ekcg.h"
+#include "kernels.cuh"
+
+using namespace ekcg;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+void set_error(const char* where, const char* what) {
+    g_last_error = std::string(where) + ": " + what;
+}
+
+#define EK_CUDA(call)                                                  \
+    do {                                                               \
+        cudaError_t e_ = (call);                                       \
+        if (e_ != cudaSuccess) {                                       \
+            set_error(#call, cudaGetErrorString(e_));                  \
+            return EKCG_ECUDA;                                         \
+        }                                                              \
+    } while (0)
+
+#define EK_TRY(expr)                    \
+    do {                                \
+        int rc_ = (expr);               \
+        if (rc_ != EKCG_OK) return rc_; \
+    } while (0)
+
+enum KClass {
+    KC_SPMM = 0, KC_GRAM, KC_REDUCE, KC_UPDATE, KC_CHOL, KC_XR, KC_RESID, KC_SPLIT, KC_PERM,
+    KC_COPY, KC_NORM, KC_MISC, KC_COUNT
+};
+const char* kClassNames[KC_COUNT] = {"spmm", "gram", "gram_reduce", "block_update", "chol_inv",
+                                     "xr_update", "residual", "split_T", "permute", "copy",
+                                     "norm", "misc"};
+
+}  // namespace
+
+// ---------------------------------------------------------------------------------------
+// Context
+// ---------------------------------------------------------------------------------------
+struct ekcg_ctx {
+    int device = 0;
+    int num_sms = 0;
+    cudaStream_t stream = nullptr;
+    ekcg_opts opts{};
+    int64_t n = 0, nnz = 0;
+    int t = 0;
+    std::vector<int64_t> perm_h;   // perm[i] = natural row at permuted position i
+
+    // permuted matrix (device)
+    int32_t* rowptr = nullptr;
+    int32_t* col = nullptr;
+    double* val = nullptr;
+    float* val32 = nullptr;
+    int32_t* perm = nullptr;       // device copy of perm (int32)
+    int32_t* dom = nullptr;        // domain of each permuted row
+    int32_t* nzmap = nullptr;      // permuted nonzero -> caller's (natural) nonzero index
+    int32_t* nat_rowptr = nullptr; // caller's row pointers (int32)
+
+    // workspace
+    int nslots = 0;                // slots per arena
+    double* W64 = nullptr;         // nslots x n x t
+    double* Z64 = nullptr;
+    float* W32 = nullptr;
+    float* Z32 = nullptr;
+    double* xb = nullptr;          // permuted x (float64)
+    double* rb = nullptr;          // permuted r
+    double* bb = nullptr;          // permuted b
+    float* x32 = nullptr;          // inner solution (FP32_IR)
+    float* r32 = nullptr;          // inner residual (FP32_IR)
+    double* nat_tmp = nullptr;     // natural-order scratch (host solve, permute)
+    double* partials = nullptr;    // Gram partials (double)
+    float* partials32 = nullptr;   // Gram partials (float)
+    double* red = nullptr;         // norm partials
+    double* C64 = nullptr;         // CGS coefficients (float64)
+    float* C32 = nullptr;          // CGS coefficients (float32)
+    double* G = nullptr;           // Gram matrix (m x m)
+    double* S = nullptr;           // Cholesky scratch
+    double* R = nullptr;
+    double* Rinv = nullptr;
+    float* Rinv32 = nullptr;
+    double* alpha = nullptr;
+    double* rho = nullptr;         // device scalars: [0] current norm, [1] scratch
+    int* flag = nullptr;           // bit 0: Cholesky breakdown
+    double* h_pinned = nullptr;    // pinned host: rho
+    int* h_flag = nullptr;         // pinned host: flag
+
+    int grid_rows = 0;             // row CTAs of the Gram kernel
+    int grid_red = 0;              // CTAs of norm-producing kernels
+    int64_t cap_coef = 0;          // elements of C64/C32
+    int64_t cap_partials = 0;      // elements of partials
+    int max_m = 0;                 // largest Gram dimension (max_s * t)
+
+    // statistics / profiling
+    int64_t launches = 0, spmm_calls = 0;
+    std::vector<cudaEvent_t> ev_pool;
+    std::vector<std::pair<int, int>> ev_used;  // (class, event index of the start)
+    double prof_ms[KC_COUNT] = {0};
+    int64_t prof_n[KC_COUNT] = {0};
+    double alg_flops[KC_COUNT] = {0};   // algorithmic flops of the last solve, per class
+    double alg_bytes[KC_COUNT] = {0};   // algorithmic (compulsory) bytes, per class
+    int64_t cls_n[KC_COUNT] = {0};      // launches per class (always counted)
+};
+
+namespace {
+
+int grid_for(const ekcg_ctx* c, int64_t work, int per_sm = 8) {
+    int64_t g = (work + kThreads - 1) / kThreads;
+    int64_t cap = (int64_t)c->num_sms * per_sm;
+    if (g > cap) g = cap;
+    if (g < 1) g = 1;
+    return (int)g;
+}
+
+// Launch helper: counts launches and brackets them with events when profiling.
+struct Launch {
+    ekcg_ctx* c;
+    int cls;
+    int idx = -1;
+    Launch(ekcg_ctx* ctx, int k, double flops = 0.0, double bytes = 0.0) : c(ctx), cls(k) {
+        c->launches++;
+        c->cls_n[k]++;
+        c->alg_flops[k] += flops;
+        c->alg_bytes[k] += bytes;
+        if (c->opts.profile) {
+            size_t need = c->ev_used.size() * 2 + 2;
+            while (c->ev_pool.size() < need) {
+                cudaEvent_t e;
+                cudaEventCreate(&e);
+                c->ev_pool.push_back(e);
+            }
+            idx = (int)c->ev_used.size() * 2;
+            cudaEventRecord(c->ev_pool[idx], c->stream);
+        }
+    }
+    ~Launch() {
+        if (idx >= 0) {
+            cudaEventRecord(c->ev_pool[idx + 1], c->stream);
+            c->ev_used.push_back({cls, idx});
+        }
+    }
+};
+
+int check_launch(const char* what) {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        set_error(what, cudaGetErrorString(e));
+        return EKCG_ECUDA;
+    }
+    return EKCG_OK;
+}
+
+template <typename T>
+MB<T> mb(T* base, int64_t stride, int first, int count, int ring, int w) {
+    return MB<T>{base, stride, first, count, ring, w};
+}
+
+template <typename T>
+MB<T> vec(T* p) { return MB<T>{p, 0, 0, 1, 1, 1}; }
+
+// ----- typed accessors --------------------------------------------------------------------
+template <typename T> struct Arena;
+template <> struct Arena<double> {
+    static double* W(ekcg_ctx* c) { return c->W64; }
+    static double* Z(ekcg_ctx* c) { return c->Z64; }
+    static const double* val(ekcg_ctx* c) { return c->val; }
+    static double* partials(ekcg_ctx* c) { return c->partials; }
+    static double* coef(ekcg_ctx* c) { return c->C64; }
+    static double* rinv(ekcg_ctx* c) { return c->Rinv; }
+};
+template <> struct Arena<float> {
+    static float* W(ekcg_ctx* c) { return c->W32; }
+    static float* Z(ekcg_ctx* c) { return c->Z32; }
+    static const float* val(ekcg_ctx* c) { return c->val32; }
+    static float* partials(ekcg_ctx* c) { return c->partials32; }
+    static float* coef(ekcg_ctx* c) { return c->C32; }
+    static float* rinv(ekcg_ctx* c) { return c->Rinv32; }
+};
+
+// ----- kernel wrappers ----------------------------------------------------------------------
+template <typename T>
+int run_spmm(ekcg_ctx* c, const T* W, T* U, int w) {
+    {
+        const double nnz = (double)c->nnz, nn = (double)c->n;
+        Launch L(c, KC_SPMM, 2.0 * nnz * w,
+                 nnz * (sizeof(T) + 4.0) + 4.0 * (nn + 1) + 2.0 * nn * w * sizeof(T));
+        k_spmm<T><<<grid_for(c, c->n * w), kThreads, 0, c->stream>>>(U, W, c->rowptr, c->col,
+                                                                    Arena<T>::val(c), c->n, w);
+    }
+    c->spmm_calls++;
+    return check_launch("k_spmm");
+}
+
+template <typename T>
+int run_split(ekcg_ctx* c, const T* r, T* out) {
+    Launch L(c, KC_SPLIT, 0.0, (double)c->n * (sizeof(T) + 4.0 + (double)c->t * sizeof(T)));
+    k_split_T<T><<<grid_for(c, c->n * c->t), kThreads, 0, c->stream>>>(out, r, c->dom, c->n,
+                                                                      c->t);
+    return check_launch("k_split_T");
+}
+
+// C[c_row0 + p, q] (ldc) = (X^T Y)[p, q]; X is chunked by the caller to <= kPMax columns.
+// The output tile shape follows Q so that no FMA is spent on padding columns.
+template <typename T, typename Acc, int TPT, int TQT, int MP, int MQ>
+int gram_shape(ekcg_ctx* c, MB<const T> X, MB<const T> Y, Acc* partials, int* ntq_out) {
+    constexpr int TP = TPT * MP, TQ = TQT * MQ;
+    const int P = X.cols(), Q = Y.cols();
+    const int ntp = (P + TP - 1) / TP, ntq = (Q + TQ - 1) / TQ;
+    const int g = c->grid_rows;
+    if ((int64_t)ntp * ntq * g * kGramTile * kGramTile > c->cap_partials) {
+        set_error("gram", "partials buffer too small");
+        return EKCG_EINVAL;
+    }
+    Launch L(c, KC_GRAM, 2.0 * (double)c->n * P * Q, (double)c->n * (P + Q) * sizeof(T));
+    dim3 grid(g, ntp * ntq);
+    k_gram_partial<T, Acc, TPT, TQT, MP, MQ><<<grid, kThreads, 0, c->stream>>>(X, Y, c->n, ntq,
+                                                                             partials);
+    *ntq_out = ntq;
+    return EKCG_OK;
+}
+
+template <typename T, typename Acc, typename Out>
+int run_gram_chunk(ekcg_ctx* c, MB<const T> X, MB<const T> Y, Out* C, int ldc, int c_row0,
+                   Acc* partials) {
+    const int P = X.cols(), Q = Y.cols();
+    int ntq = 1, TP = 64, TQ = 64;
+    if (Q > 32) {
+        EK_TRY((gram_shape<T, Acc, 16, 16, 4, 4>(c, X, Y, partials, &ntq)));
+    } else if (Q > 16) {
+        TQ = 32;
+        EK_TRY((gram_shape<T, Acc, 32, 8, 2, 4>(c, X, Y, partials, &ntq)));
+    } else if (Q > 4) {
+        TQ = 16;
+        EK_TRY((gram_shape<T, Acc, 64, 4, 1, 4>(c, X, Y, partials, &ntq)));
+    } else if (Q > 1) {
+        TQ = 4;
+        EK_TRY((gram_shape<T, Acc, 64, 4, 1, 1>(c, X, Y, partials, &ntq)));
+    } else {
+        TP = 64;
+        TQ = 1;
+        if (P > 64) {
+            TP = 256;
+            EK_TRY((gram_shape<T, Acc, 256, 1, 1, 1>(c, X, Y, partials, &ntq)));
+        } else {
+            EK_TRY((gram_shape<T, Acc, 64, 4, 1, 1>(c, X, Y, partials, &ntq)));
+            TQ = 4;
+        }
+    }
+    EK_TRY(check_launch("k_gram_partial"));
+    const int g = c->grid_rows;
+    {
+        Launch L(c, KC_REDUCE, (double)g * P * Q, (double)g * P * Q * sizeof(Acc));
+        int tot = P * Q;
+        int gr = std::max(1, std::min((tot + kThreads - 1) / kThreads, c->num_sms * 4));
+        k_gram_reduce<Acc, Out><<<gr, kThreads, 0, c->stream>>>(partials, g, ntq, TP, TQ, P, Q,
+                                                                C, ldc, c_row0);
+    }
+    return check_launch("k_gram_reduce");
+}
+
+// C (P x Q, ldc = Q) = X^T Y for any number of X blocks.
+template <typename T, typename Acc, typename Out>
+int run_gram(ekcg_ctx* c, MB<const T> X, MB<const T> Y, Out* C, Acc* partials) {
+    const int Q = Y.cols();
+    const int per = std::max(1, kPMax / X.w);
+    for (int b0 = 0; b0 < X.count; b0 += per) {
+        MB<const T> Xc = X;
+        Xc.first = (X.first + b0) % X.ring;
+        Xc.count = std::min(per, X.count - b0);
+        EK_TRY((run_gram_chunk<T, Acc, Out>(c, Xc, Y, C, Q, b0 * X.w, partials)));
+    }
+    return EKCG_OK;
+}
+
+template <typename T, typename CT>
+int run_update_chunk(ekcg_ctx* c, MB<const T> X, const CT* C, int ldc, int c_row0,
+                     MB<const T> Y, MB<T> OUT, int beta_on, CT alpha, int upper) {
+    const int P = X.cols();
+    size_t smem = (size_t)kUpdRows * (P + 1) * sizeof(T);
+    int g = (int)std::min<int64_t>((c->n + kUpdRows - 1) / kUpdRows, (int64_t)c->num_sms * 4);
+    {
+        const int Qo = OUT.cols();
+        const double fl = upper ? (double)c->n * P * (P + 1) : 2.0 * (double)c->n * P * Qo;
+        const double by = (double)c->n * (P + (beta_on ? 2 : 1) * Qo) * sizeof(T);
+        Launch L(c, KC_UPDATE, fl, by);
+        k_update<T, CT><<<g, kThreads, smem, c->stream>>>(X, C, ldc, c_row0, Y, OUT, c->n,
+                                                          beta_on, alpha, upper);
+    }
+    return check_launch("k_update");
+}
+
+// OUT = Y - X C  (C is X.cols() x OUT.cols(), ldc = OUT.cols()); X chunked by kPMax columns.
+template <typename T, typename CT>
+int run_sub(ekcg_ctx* c, MB<const T> X, const CT* C, MB<const T> Y, MB<T> OUT) {
+    const int per = std::max(1, kPMax / X.w);
+    const int Q = OUT.cols();
+    for (int b0 = 0; b0 < X.count; b0 += per) {
+        MB<const T> Xc = X;
+        Xc.first = (X.first + b0) % X.ring;
+        Xc.count = std::min(per, X.count - b0);
+        MB<const T> Yc = (b0 == 0) ? Y : as_const(OUT);
+        EK_TRY((run_update_chunk<T, CT>(c, Xc, C, Q, b0 * X.w, Yc, OUT, 1, CT(-1), 0)));
+    }
+    return EKCG_OK;
+}
+
+// X <- X Rinv in place (Rinv upper triangular m x m, m = X.cols() <= kPMax).
+template <typename T, typename CT>
+int run_rmul(ekcg_ctx* c, MB<T> X, const CT* Rinv) {
+    return run_update_chunk<T, CT>(c, as_const(X), Rinv, X.cols(), 0, as_const(X), X, 0, CT(1),
+                                   1);
+}
+
+int run_chol(ekcg_ctx* c, int m) {
+    Launch L(c, KC_CHOL);
+    k_chol_inv<<<1, 512, 0, c->stream>>>(c->G, m, c->S, c->R, c->Rinv, c->opts.breakdown_tol,
+                                         c->flag);
+    return check_launch("k_chol_inv");
+}
+
+template <typename T>
+int run_copy(ekcg_ctx* c, T* dst, const T* src, int64_t count) {
+    Launch L(c, KC_COPY);
+    EK_CUDA(cudaMemcpyAsync(dst, src, count * sizeof(T), cudaMemcpyDeviceToDevice, c->stream));
+    return EKCG_OK;
+}
+
+// Convert the float64 Rinv to the basis precision when needed.
+__global__ void k_d2f(float* __restrict__ y, const double* __restrict__ x, int m) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x)
+        y[i] = (float)x[i];
+}
+
+template <typename T> const T* rinv_for(ekcg_ctx* c, int m);
+template <> const double* rinv_for<double>(ekcg_ctx* c, int) { return c->Rinv; }
+template <> const float* rinv_for<float>(ekcg_ctx* c, int m) {
+    k_d2f<<<std::max(1, std::min((m * m + 255) / 256, 1024)), 256, 0, c->stream>>>(c->Rinv32,
+                                                                                   c->Rinv, m * m);
+    c->launches++;
+    return c->Rinv32;
+}
+
+int sync_read(ekcg_ctx* c, double* rho, int* flag) {
+    EK_CUDA(cudaMemcpyAsync(c->h_pinned, c->rho, sizeof(double), cudaMemcpyDeviceToHost,
+                            c->stream));
+    EK_CUDA(cudaMemcpyAsync(c->h_flag, c->flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    EK_CUDA(cudaStreamSynchronize(c->stream));
+    *rho = c->h_pinned[0];
+    *flag = c->h_flag[0];
+    return EKCG_OK;
+}
+
+// ---------------------------------------------------------------------------------------
+// The s-step solver on the permuted system, basis precision T.
+// Solves A y = rhs with y starting from the content of `x` (T), residual in `r` (T).
+// ---------------------------------------------------------------------------------------
+template <typename T>
+struct Engine {
+    ekcg_ctx* c;
+    int s, t;
+    int64_t n, slot;                 // slot = n*t elements
+    T* Wb;
+    T* Zb;
+    T* x;
+    T* r;
+    int ring;                        // W slots in use (window or full history)
+    int zring;                       // Z slots: the s blocks of V plus the candidate
+    int64_t nblocks = 0;             // t-blocks created so far (global numbering)
+
+    Engine(ekcg_ctx* ctx, int s_, T* x_, T* r_)
+        : c(ctx), s(s_), t(ctx->t), n(ctx->n), slot(ctx->n * ctx->t), Wb(Arena<T>::W(ctx)),
+          Zb(Arena<T>::Z(ctx)), x(x_), r(r_) {
+        const int v = c->opts.variant, bs = c->opts.basis;
+        if (bs == EKCG_SSTEP)
+            ring = (v == EKCG_SRE) ? s + 2 : c->nslots;
+        else
+            ring = (v == EKCG_SRE) ? 2 * s + 1 : c->nslots;
+        if (ring > c->nslots) ring = c->nslots;
+        zring = s + 1;
+    }
+    bool full_history() const { return !(c->opts.variant == EKCG_SRE); }
+    T* W(int64_t j) { return Wb + (int64_t)(j % ring) * slot; }
+    T* Z(int64_t j) { return Zb + (int64_t)(j % zring) * slot; }
+    // blocks [j0, j0+cnt)
+    MB<T> Wm(int64_t j0, int cnt) { return mb<T>(Wb, slot, (int)(j0 % ring), cnt, ring, t); }
+    MB<T> Zm(int64_t j0, int cnt) { return mb<T>(Zb, slot, (int)(j0 % zring), cnt, zring, t); }
+    bool fits(int64_t upto) const { return upto <= (int64_t)ring; }
+
+    // Z = A W for the blocks [j, j+cnt).
+    int products(int64_t j, int cnt) {
+        for (int i = 0; i < cnt; ++i) EK_TRY(run_spmm<T>(c, W(j + i), Z(j + i), t));
+        return EKCG_OK;
+    }
+
+    // CGS2 of blocks [j, j+cnt) against Q = W blocks [q0, q0+qc): two passes of
+    // C = Q^T (A W), W <- W - Q C, each A W a fresh sparse product; on entry Z holds A W of
+    // the input (`cand` if non-null, else W(j..)), on exit Z = A W of the output.
+    int cgs2(int64_t j, int cnt, int64_t q0, int qc, const T* cand) {
+        if (qc <= 0) {
+            if (cand) EK_TRY(run_copy<T>(c, W(j), cand, slot));
+            return EKCG_OK;
+        }
+        T* C = Arena<T>::coef(c);
+        const int P = qc * t, Qn = cnt * t;
+        if ((int64_t)P * Qn > c->cap_coef) {
+            set_error("cgs2", "coefficient buffer too small");
+            return EKCG_ENOMEM;
+        }
+        for (int pass = 0; pass < 2; ++pass) {
+            EK_TRY((run_gram<T, T, T>(c, as_const(Wm(q0, qc)), as_const(Zm(j, cnt)), C,
+                                      Arena<T>::partials(c))));
+            MB<const T> Win = (pass == 0 && cand) ? mb<const T>(cand, 0, 0, 1, 1, t)
+                                                  : as_const(Wm(j, cnt));
+            EK_TRY((run_sub<T, T>(c, as_const(Wm(q0, qc)), C, Win, Wm(j, cnt))));
+            EK_TRY(products(j, cnt));
+        }
+        return EKCG_OK;
+    }
+
+    // A-CholQR (or Pre-CholQR) of blocks [j, j+cnt) viewed as one n x (cnt t) matrix, with
+    // Z = A W on entry; A W is carried through the triangular factors.
+    int self_orth(int64_t j, int cnt) {
+        const int m = cnt * t;
+        if (c->opts.orth == EKCG_PRECHOLQR) {
+            // Euclidean CholQR2: W = Z S, applied to W and A W alike.
+            for (int rep = 0; rep < 2; ++rep) {
+                EK_TRY((run_gram<T, double, double>(c, as_const(Wm(j, cnt)),
+                                                    as_const(Wm(j, cnt)), c->G, c->partials)));
+                EK_TRY(run_chol(c, m));
+                const T* Ri = rinv_for<T>(c, m);
+                EK_TRY((run_rmul<T, T>(c, Wm(j, cnt), Ri)));
+                EK_TRY((run_rmul<T, T>(c, Zm(j, cnt), Ri)));
+            }
+        }
+        EK_TRY((run_gram<T, double, double>(c, as_const(Wm(j, cnt)), as_const(Zm(j, cnt)), c->G,
+                                            c->partials)));
+        EK_TRY(run_chol(c, m));
+        const T* Ri = rinv_for<T>(c, m);
+        EK_TRY((run_rmul<T, T>(c, Wm(j, cnt), Ri)));
+        EK_TRY((run_rmul<T, T>(c, Zm(j, cnt), Ri)));
+        return EKCG_OK;
+    }
+
+    // Q window for block j (SRE: W_{j-2}, W_{j-1} that exist; full: all previous).
+    void window(int64_t j, int64_t* q0, int* qc) const {
+        if (full_history()) {
+            *q0 = 0;
+            *qc = (int)j;
+        } else {
+            *q0 = std::max<int64_t>(0, j - 2);
+            *qc = (int)(j - *q0);
+        }
+    }
+
+    // Iteration k (1-based) of Algorithms 3 / 4 / 6; returns the first block of V.
+    int iterate_sstep(int k, const T* r0_for_T, int64_t* v0) {
+        const int v = c->opts.variant;
+        const int64_t j0 = nblocks;
+        *v0 = j0;
+        if (full_history() && !fits(j0 + s)) {
+            set_error("solve", "stored basis capacity (max_blocks) exceeded");
+            return EKCG_ENOMEM;
+        }
+        for (int i = 0; i < s; ++i) {
+            const int64_t j = j0 + i;
+            if ((v == EKCG_MSDO && i == 0) || (v != EKCG_MSDO && j == 0)) {
+                // W = T(r_{k-1}) (MSDO, against all previous blocks) or T(r_0)
+                EK_TRY(run_split<T>(c, v == EKCG_MSDO ? r : r0_for_T, W(j)));
+                EK_TRY(run_spmm<T>(c, W(j), Z(j), t));
+                EK_TRY(cgs2(j, 1, 0, v == EKCG_MSDO ? (int)j : 0, nullptr));
+            } else {
+                // W_j = A W_{j-1}: the product carried with the previous block
+                const T* cand = Z(j - 1);
+                EK_TRY(run_spmm<T>(c, cand, Z(j), t));
+                int64_t q0;
+                int qc;
+                window(j, &q0, &qc);
+                EK_TRY(cgs2(j, 1, q0, qc, cand));
+            }
+            EK_TRY(self_orth(j, 1));
+            nblocks = j + 1;
+        }
+        (void)k;
+        return EKCG_OK;
+    }
+
+    // Iteration k of the CA forms (Algorithm 5 / Algorithm 7).
+    int iterate_ca(int k, const T* r0_for_T, int64_t* v0) {
+        const int v = c->opts.variant;
+        const bool alg7 = c->opts.basis == EKCG_CA7;
+        const int64_t j0 = nblocks;
+        *v0 = j0;
+        if (full_history() && !fits(j0 + s)) {
+            set_error("solve", "stored basis capacity (max_blocks) exceeded");
+            return EKCG_ENOMEM;
+        }
+        int64_t q0;
+        int qc;
+        if (v == EKCG_SRE) {
+            q0 = std::max<int64_t>(0, j0 - (s + 1));
+            qc = (int)(j0 - q0);
+        } else {
+            q0 = 0;
+            qc = (int)j0;
+        }
+        // first block W_j: T(r_{k-1}) (MSDO), T(r_0) (k = 1) or A W_{j-1}
+        const T* cand = nullptr;
+        if (v == EKCG_MSDO) {
+            EK_TRY(run_split<T>(c, r, W(j0)));
+        } else if (k == 1) {
+            EK_TRY(run_split<T>(c, r0_for_T, W(j0)));
+        } else {
+            cand = Z(j0 - 1);
+        }
+        EK_TRY(run_spmm<T>(c, cand ? cand : W(j0), Z(j0), t));
+        if (alg7) {
+            if (k > 1) {
+                EK_TRY(cgs2(j0, 1, q0, qc, cand));
+            } else if (cand) {
+                EK_TRY(run_copy<T>(c, W(j0), cand, slot));
+            }
+            EK_TRY(self_orth(j0, 1));
+        } else if (cand) {
+            EK_TRY(run_copy<T>(c, W(j0), cand, slot));
+        }
+        // powers W_{j+i} = A W_{j+i-1}
+        for (int i = 1; i < s; ++i) {
+            const int64_t j = j0 + i;
+            EK_TRY(run_copy<T>(c, W(j), Z(j - 1), slot));
+            EK_TRY(run_spmm<T>(c, W(j), Z(j), t));
+        }
+        if (k > 1) EK_TRY(cgs2(j0, s, q0, qc, nullptr));
+        EK_TRY(self_orth(j0, s));
+        nblocks = j0 + s;
+        return EKCG_OK;
+    }
+
+    // alpha = V^T r, x += V alpha, r -= (A V) alpha, rho = ||r||.
+    int update(int64_t v0) {
+        EK_TRY((run_gram<T, double, double>(c, as_const(Wm(v0, s)), mb<const T>(r, 0, 0, 1, 1, 1),
+                                            c->alpha, c->partials)));
+        {
+            const double nn = (double)n, stc = (double)s * t;
+            Launch L(c, KC_XR, 4.0 * nn * stc + 2.0 * nn, nn * (2.0 * stc + 4.0) * sizeof(T));
+            k_xr_update<T><<<c->grid_red, kThreads, 0, c->stream>>>(
+                x, r, as_const(Wm(v0, s)), as_const(Zm(v0, s)), c->alpha, n, c->red, c->flag);
+        }
+        EK_TRY(check_launch("k_xr_update"));
+        {
+            Launch L(c, KC_NORM);
+            k_norm_finalize<<<1, 32, 0, c->stream>>>(c->red, c->grid_red, c->rho);
+        }
+        return check_launch("k_norm_finalize");
+    }
+};
+
+// ||v||_2 of a device vector of T into c->rho[0] (reuses the xr_update reduction layout).
+template <typename T>
+__global__ void k_sumsq(const T* __restrict__ v, int64_t n, double* __restrict__ partials) {
+    __shared__ double red[32];
+    double local = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        local += (double)v[i] * (double)v[i];
+    const double s = block_sum(local, red);
+    if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
+template <typename T>
+int run_norm(ekcg_ctx* c, const T* v) {
+    {
+        Launch L(c, KC_NORM);
+        k_sumsq<T><<<c->grid_red, kThreads, 0, c->stream>>>(v, c->n, c->red);
+    }
+    EK_TRY(check_launch("k_sumsq"));
+    Launch L(c, KC_NORM);
+    k_norm_finalize<<<1, 32, 0, c->stream>>>(c->red, c->grid_red, c->rho);
+    return check_launch("k_norm_finalize");
+}
+
+// The enlarged s-step loop on the permuted system in precision T.
+//   x: initial guess / solution (T), r: residual b - A x on entry (T), rho0 = ||r||.
+//   hist: receives rho_1.. (not rho_0) up to cap; returns status; *iters iterations done.
+//   rho_start = ||r|| on entry; the loop runs while rho > tol_abs and k < maxit + 1.
+//   T(r_0) is taken only in iteration 1, before the first update, so r itself serves.
+template <typename T>
+int sstep_loop(ekcg_ctx* c, int s, double tol_abs, int maxit, T* x, T* r, double rho_start,
+               double* hist, int cap, int* hlen, int* iters) {
+    Engine<T> E(c, s, x, r);
+    int k = 1;
+    double rho = rho_start;
+    int status = EKCG_OK;
+    *iters = 0;
+    int flag = 0;
+    while (rho > tol_abs && k < maxit + 1) {
+        int64_t v0 = 0;
+        int rc = (c->opts.basis == EKCG_SSTEP) ? E.iterate_sstep(k, r, &v0)
+                                               : E.iterate_ca(k, r, &v0);
+        if (rc != EKCG_OK) return rc;
+        EK_TRY(E.update(v0));
+        EK_TRY(sync_read(c, &rho, &flag));
+        if (flag & 1) {
+            status = EKCG_EBREAKDOWN;
+            break;
+        }
+        if (*hlen < cap && hist) hist[*hlen] = rho;
+        (*hlen)++;
+        *iters = k;
+        k++;
+    }
+    if (status == EKCG_OK && rho > tol_abs) status = EKCG_MAXIT;
+    return status;
+}
+
+int validate_and_setup(int64_t n, const int64_t* rowptr, const int32_t* colind,
+                       const double* val, int t, const int32_t* part, ekcg_ctx* c) {
+    if (n <= 0 || n > (int64_t)INT32_MAX - 1 || t < 1 || t > 256 || !rowptr || !colind || !val ||
+        !part) {
+        set_error("ekcg_setup", "bad sizes or null pointers");
+        return EKCG_EINVAL;
+    }
+    if (rowptr[0] != 0) {
+        set_error("ekcg_setup", "rowptr[0] != 0");
+        return EKCG_EINVAL;
+    }
+    for (int64_t i = 0; i < n; ++i)
+        if (rowptr[i + 1] < rowptr[i]) {
+            set_error("ekcg_setup", "rowptr not monotone");
+            return EKCG_EINVAL;
+        }
+    const int64_t nnz = rowptr[n];
+    if (nnz > (int64_t)INT32_MAX) {
+        set_error("ekcg_setup", "nnz exceeds int32");
+        return EKCG_EINVAL;
+    }
+    std::vector<int64_t> cnt(t, 0);
+    for (int64_t i = 0; i < n; ++i) {
+        if (part[i] < 0 || part[i] >= t) {
+            set_error("ekcg_setup", "part out of range");
+            return EKCG_EINVAL;
+        }
+        cnt[part[i]]++;
+        bool diag = false;
+        for (int64_t j = rowptr[i]; j < rowptr[i + 1]; ++j) {
+            const int32_t cj = colind[j];
+            if (cj < 0 || cj >= n || (j > rowptr[i] && colind[j - 1] >= cj)) {
+                set_error("ekcg_setup", "column index out of range or not sorted/unique");
+                return EKCG_EINVAL;
+            }
+            if (!std::isfinite(val[j])) {
+                set_error("ekcg_setup", "non-finite matrix value");
+                return EKCG_EINVAL;
+            }
+            if (cj == i) {
+                diag = true;
+                if (!(val[j] > 0)) {
+                    set_error("ekcg_setup", "non-positive diagonal");
+                    return EKCG_EINVAL;
+                }
+            }
+            // structural symmetry: (cj, i) must exist
+            const int32_t* b = colind + rowptr[cj];
+            const int32_t* e = colind + rowptr[cj + 1];
+            if (!std::binary_search(b, e, (int32_t)i)) {
+                set_error("ekcg_setup", "matrix is not structurally symmetric");
+                return EKCG_EINVAL;
+            }
+        }
+        if (!diag) {
+            set_error("ekcg_setup", "missing diagonal entry");
+            return EKCG_EINVAL;
+        }
+    }
+    for (int d = 0; d < t; ++d)
+        if (cnt[d] == 0) {
+            set_error("ekcg_setup", "empty domain");
+            return EKCG_EINVAL;
+        }
+    c->n = n;
+    c->nnz = nnz;
+    c->t = t;
+    // stable counting sort of rows by domain (Section 4 reordering)
+    std::vector<int64_t> start(t + 1, 0);
+    for (int d = 0; d < t; ++d) start[d + 1] = start[d] + cnt[d];
+    c->perm_h.assign(n, 0);
+    std::vector<int64_t> pos(start.begin(), start.end() - 1);
+    for (int64_t i = 0; i < n; ++i) c->perm_h[pos[part[i]]++] = i;
+    std::vector<int32_t> iperm(n);
+    for (int64_t i = 0; i < n; ++i) iperm[c->perm_h[i]] = (int32_t)i;
+    // permuted CSR: row i of P A P^T is row perm[i] of A with columns iperm[.], re-sorted
+    std::vector<int32_t> prow(n + 1), pcol(nnz), dom(n), perm32(n), nzmap(nnz), nrow(n + 1);
+    std::vector<double> pval(nnz);
+    prow[0] = 0;
+    for (int64_t i = 0; i <= n; ++i) nrow[i] = (int32_t)rowptr[i];
+    std::vector<std::pair<int32_t, int32_t>> tmp;   // (permuted column, natural nnz index)
+    for (int64_t i = 0; i < n; ++i) {
+        const int64_t src = c->perm_h[i];
+        perm32[i] = (int32_t)src;
+        dom[i] = part[src];
+        tmp.clear();
+        for (int64_t j = rowptr[src]; j < rowptr[src + 1]; ++j)
+            tmp.push_back({iperm[colind[j]], (int32_t)j});
+        std::sort(tmp.begin(), tmp.end());
+        int64_t o = prow[i];
+        for (auto& pr : tmp) {
+            pcol[o] = pr.first;
+            pval[o] = val[pr.second];
+            nzmap[o] = pr.second;
+            ++o;
+        }
+        prow[i + 1] = (int32_t)o;
+    }
+    std::vector<float> pval32(nnz);
+    for (int64_t j = 0; j < nnz; ++j) pval32[j] = (float)pval[j];
+    EK_CUDA(cudaMalloc(&c->rowptr, (n + 1) * sizeof(int32_t)));
+    EK_CUDA(cudaMalloc(&c->col, std::max<int64_t>(nnz, 1) * sizeof(int32_t)));
+    EK_CUDA(cudaMalloc(&c->val, std::max<int64_t>(nnz, 1) * sizeof(double)));
+    EK_CUDA(cudaMalloc(&c->val32, std::max<int64_t>(nnz, 1) * sizeof(float)));
+    EK_CUDA(cudaMalloc(&c->perm, n * sizeof(int32_t)));
+    EK_CUDA(cudaMalloc(&c->dom, n * sizeof(int32_t)));
+    EK_CUDA(cudaMemcpy(c->rowptr, prow.data(), (n + 1) * sizeof(int32_t), cudaMemcpyHostToDevice));
+    EK_CUDA(cudaMemcpy(c->col, pcol.data(), nnz * sizeof(int32_t), cudaMemcpyHostToDevice));
+    EK_CUDA(cudaMemcpy(c->val, pval.data(), nnz * sizeof(double), cudaMemcpyHostToDevice));
+    EK_CUDA(cudaMemcpy(c->val32, pval32.data(), nnz * sizeof(float), cudaMemcpyHostToDevice));
+    EK_CUDA(cudaMemcpy(c->perm, perm32.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice));
+    EK_CUDA(cudaMemcpy(c->dom, dom.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice));
+    EK_CUDA(cudaMalloc(&c->nzmap, std::max<int64_t>(nnz, 1) * sizeof(int32_t)));
+    EK_CUDA(cudaMalloc(&c->nat_rowptr, (n + 1) * sizeof(int32_t)));
+    EK_CUDA(cudaMemcpy(c->nzmap, nzmap.data(), nnz * sizeof(int32_t), cudaMemcpyHostToDevice));
+    EK_CUDA(cudaMemcpy(c->nat_rowptr, nrow.data(), (n + 1) * sizeof(int32_t),
+                       cudaMemcpyHostToDevice));
+    return EKCG_OK;
+}
+
+int alloc_workspace(ekcg_ctx* c) {
+    const int64_t n = c->n;
+    const int t = c->t, S = c->opts.max_s;
+    const bool f32 = c->opts.precision == EKCG_FP32_IR;
+    const size_t esz = f32 ? sizeof(float) : sizeof(double);
+    const int64_t slot_bytes = n * t * (int64_t)esz;   // one stored W block
+    const bool full = c->opts.variant != EKCG_SRE;
+    int nslots;
+    if (!full) {
+        nslots = (c->opts.basis == EKCG_SSTEP) ? S + 2 : 2 * S + 1;
+    } else if (c->opts.max_blocks > 0) {
+        nslots = c->opts.max_blocks;
+    } else {
+        int64_t budget = c->opts.max_basis_bytes;
+        if (budget <= 0) {
+            size_t fr = 0, tot = 0;
+            EK_CUDA(cudaMemGetInfo(&fr, &tot));
+            budget = (int64_t)(fr * 0.4);
+        }
+        nslots = (int)std::min<int64_t>(budget / slot_bytes, 1 << 20);
+    }
+    if (nslots < S + 2) nslots = S + 2;
+    c->nslots = nslots;
+    const int zslots = S + 1;   // A W of the s blocks of V and of the candidate block
+    c->max_m = S * t;
+    c->grid_rows = (int)std::max<int64_t>(
+        1, std::min<int64_t>((n + kGramRows - 1) / kGramRows, (int64_t)c->num_sms * 2));
+    c->grid_red = grid_for(c, n, 4);
+    const int ntile = (std::max(kPMax, c->max_m) + kGramTile - 1) / kGramTile;
+    const int ntq = (c->max_m + kGramTile - 1) / kGramTile;
+    c->cap_partials = (int64_t)ntile * ntq * c->grid_rows * kGramTile * kGramTile;
+    // coefficients: (stored columns) x (s t)
+    const int64_t qcols = full ? (int64_t)nslots * t : (int64_t)(2 * S + 1) * t;
+    c->cap_coef = qcols * c->max_m;
+    if (f32) {
+        EK_CUDA(cudaMalloc(&c->W32, (size_t)nslots * n * t * sizeof(float)));
+        EK_CUDA(cudaMalloc(&c->Z32, (size_t)zslots * n * t * sizeof(float)));
+        EK_CUDA(cudaMalloc(&c->partials32, c->cap_partials * sizeof(float)));
+        EK_CUDA(cudaMalloc(&c->C32, c->cap_coef * sizeof(float)));
+        EK_CUDA(cudaMalloc(&c->Rinv32, (size_t)c->max_m * c->max_m * sizeof(float)));
+        EK_CUDA(cudaMalloc(&c->x32, n * sizeof(float)));
+        EK_CUDA(cudaMalloc(&c->r32, n * sizeof(float)));
+    } else {
+        EK_CUDA(cudaMalloc(&c->W64, (size_t)nslots * n * t * sizeof(double)));
+        EK_CUDA(cudaMalloc(&c->Z64, (size_t)zslots * n * t * sizeof(double)));
+        EK_CUDA(cudaMalloc(&c->C64, c->cap_coef * sizeof(double)));
+    }
+    EK_CUDA(cudaMalloc(&c->partials, c->cap_partials * sizeof(double)));
+    EK_CUDA(cudaMalloc(&c->xb, n * sizeof(double)));
+    EK_CUDA(cudaMalloc(&c->rb, n * sizeof(double)));
+    EK_CUDA(cudaMalloc(&c->bb, n * sizeof(double)));
+    EK_CUDA(cudaMalloc(&c->nat_tmp, 2 * n * sizeof(double)));
+    EK_CUDA(cudaMalloc(&c->red, std::max(c->grid_red, 1024) * sizeof(double)));
+    const size_t mm = (size_t)c->max_m * c->max_m;
+    EK_CUDA(cudaMalloc(&c->G, mm * sizeof(double)));
+    EK_CUDA(cudaMalloc(&c->S, mm * sizeof(double)));
+    EK_CUDA(cudaMalloc(&c->R, mm * sizeof(double)));
+    EK_CUDA(cudaMalloc(&c->Rinv, mm * sizeof(double)));
+    EK_CUDA(cudaMalloc(&c->alpha, c->max_m * sizeof(double)));
+    EK_CUDA(cudaMalloc(&c->rho, 4 * sizeof(double)));
+    EK_CUDA(cudaMalloc(&c->flag, sizeof(int)));
+    EK_CUDA(cudaMallocHost(&c->h_pinned, 4 * sizeof(double)));
+    EK_CUDA(cudaMallocHost(&c->h_flag, sizeof(int)));
+    EK_CUDA(cudaFuncSetAttribute(k_update<double, double>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(kUpdRows * (kPMax + 1) * sizeof(double))));
+    EK_CUDA(cudaFuncSetAttribute(k_update<float, float>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(kUpdRows * (kPMax + 1) * sizeof(float))));
+    return EKCG_OK;
+}
+
+void free_ctx(ekcg_ctx* c) {
+    void* ptrs[] = {c->rowptr, c->col, c->val, c->val32, c->perm, c->dom, c->nzmap,
+                    c->nat_rowptr, c->W64, c->Z64,
+                    c->W32, c->Z32, c->xb, c->rb, c->bb, c->x32, c->r32, c->nat_tmp,
+                    c->partials, c->partials32, c->red, c->C64, c->C32, c->G, c->S, c->R,
+                    c->Rinv, c->Rinv32, c->alpha, c->rho, c->flag};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    if (c->h_pinned) cudaFreeHost(c->h_pinned);
+    if (c->h_flag) cudaFreeHost(c->h_flag);
+    for (auto e : c->ev_pool) cudaEventDestroy(e);
+}
+
+int collect_profile(ekcg_ctx* c) {
+    for (int i = 0; i < KC_COUNT; ++i) {
+        c->prof_ms[i] = 0;
+        c->prof_n[i] = 0;
+    }
+    if (!c->opts.profile || c->ev_used.empty()) return EKCG_OK;
+    EK_CUDA(cudaStreamSynchronize(c->stream));
+    for (auto& u : c->ev_used) {
+        float ms = 0.f;
+        EK_CUDA(cudaEventElapsedTime(&ms, c->ev_pool[u.second], c->ev_pool[u.second + 1]));
+        c->prof_ms[u.first] += ms;
+        c->prof_n[u.first]++;
+    }
+    c->ev_used.clear();
+    return EKCG_OK;
+}
+
+// Core solve on device buffers (natural order b, x0, x).
+int solve_device(ekcg_ctx* c, const double* b, const double* x0, int s, double tol, int maxit,
+                 double* x, int* iters, double* hist, int cap, int* hlen) {
+    const int64_t n = c->n;
+    c->launches = 0;
+    c->spmm_calls = 0;
+    c->ev_used.clear();
+    for (int i = 0; i < KC_COUNT; ++i) {
+        c->alg_flops[i] = 0;
+        c->alg_bytes[i] = 0;
+        c->cls_n[i] = 0;
+    }
+    int hl = 0, it = 0;
+    // permute b, x0 into the domain order
+    {
+        Launch L(c, KC_PERM);
+        k_gather<double><<<grid_for(c, n), kThreads, 0, c->stream>>>(c->bb, b, c->perm, n);
+    }
+    EK_TRY(check_launch("k_gather"));
+    if (x0) {
+        Launch L(c, KC_PERM);
+        k_gather<double><<<grid_for(c, n), kThreads, 0, c->stream>>>(c->xb, x0, c->perm, n);
+    } else {
+        Launch L(c, KC_MISC);
+        k_fill<double><<<grid_for(c, n), kThreads, 0, c->stream>>>(c->xb, 0.0, n);
+    }
+    EK_TRY(check_launch("x0"));
+    EK_CUDA(cudaMemsetAsync(c->flag, 0, sizeof(int), c->stream));
+    // r_0 = b - A x_0, rho_0 = ||r_0||
+    {
+        Launch L(c, KC_RESID, 2.0 * c->nnz + 3.0 * n,
+                 12.0 * c->nnz + 4.0 * (n + 1) + 8.0 * 3 * n);
+        k_residual<<<c->grid_red, kThreads, 0, c->stream>>>(c->rb, c->bb, c->xb, c->rowptr,
+                                                            c->col, c->val, n, c->red);
+    }
+    EK_TRY(check_launch("k_residual"));
+    {
+        Launch L(c, KC_NORM);
+        k_norm_finalize<<<1, 32, 0, c->stream>>>(c->red, c->grid_red, c->rho);
+    }
+    double rho0 = 0;
+    int flag = 0;
+    EK_TRY(sync_read(c, &rho0, &flag));
+    if (!std::isfinite(rho0)) {
+        set_error("ekcg_solve", "non-finite right-hand side or initial guess");
+        return EKCG_EINVAL;
+    }
+    if (hist && cap > 0) hist[0] = rho0;
+    hl = 1;
+    int status = EKCG_OK;
+    if (rho0 > 0 && !(rho0 > tol * rho0)) {
+        // tol >= 1: the while condition fails before the first iteration
+    } else if (rho0 > 0 && maxit == 0) {
+        status = EKCG_MAXIT;
+    } else if (rho0 > 0) {
+        const double tol_abs = tol * rho0;
+        if (c->opts.precision == EKCG_FP64) {
+            status = sstep_loop<double>(c, s, tol_abs, maxit, c->xb, c->rb, rho0, hist, cap,
+                                        &hl, &it);
+        } else {
+            // float64 iterative refinement around float32 s-step inner solves
+            double rho = rho0;
+            int total = 0;
+            status = EKCG_MAXIT;
+            for (int ref = 0; ref < c->opts.max_refine && total < maxit; ++ref) {
+                // r (float64) is current and rho[0] = ||r||; keep that norm in rho[1] (the
+                // inner loop overwrites rho[0]) and solve A d = r / ||r|| in float32.
+                EK_CUDA(cudaMemcpyAsync(c->rho + 1, c->rho, sizeof(double),
+                                        cudaMemcpyDeviceToDevice, c->stream));
+                {
+                    Launch L(c, KC_MISC);
+                    k_to_float_scaled<<<grid_for(c, n), kThreads, 0, c->stream>>>(c->r32, c->rb,
+                                                                                 c->rho + 1, n);
+                    k_fill<float><<<grid_for(c, n), kThreads, 0, c->stream>>>(c->x32, 0.f, n);
+                }
+                EK_CUDA(cudaMemsetAsync(c->flag, 0, sizeof(int), c->stream));
+                int in_it = 0, in_hl = 0;
+                int rc = sstep_loop<float>(c, s, c->opts.inner_tol, maxit - total, c->x32,
+                                           c->r32, 1.0, nullptr, 0, &in_hl, &in_it);
+                total += in_it;
+                if (rc == EKCG_EBREAKDOWN && in_it == 0) {
+                    status = EKCG_EBREAKDOWN;
+                    break;
+                }
+                if (rc < 0 && rc != EKCG_EBREAKDOWN) return rc;
+                {
+                    Launch L(c, KC_MISC);
+                    k_axpy_scaled<<<grid_for(c, n), kThreads, 0, c->stream>>>(c->xb, c->x32,
+                                                                             c->rho + 1, n);
+                }
+                EK_TRY(check_launch("k_axpy_scaled"));
+                {
+                    Launch L(c, KC_RESID);
+                    k_residual<<<c->grid_red, kThreads, 0, c->stream>>>(
+                        c->rb, c->bb, c->xb, c->rowptr, c->col, c->val, n, c->red);
+                }
+                {
+                    Launch L(c, KC_NORM);
+                    k_norm_finalize<<<1, 32, 0, c->stream>>>(c->red, c->grid_red, c->rho);
+                }
+                EK_TRY(sync_read(c, &rho, &flag));
+                if (hist && hl < cap) hist[hl] = rho;
+                hl++;
+                if (!(rho > tol_abs)) {
+                    status = EKCG_OK;
+                    break;
+                }
+                if (!std::isfinite(rho)) {
+                    status = EKCG_EBREAKDOWN;
+                    break;
+                }
+            }
+            it = total;
+        }
+        if (status < 0 && status != EKCG_EBREAKDOWN && status != EKCG_ENOMEM) return status;
+    }
+    {
+        Launch L(c, KC_PERM);
+        k_scatter<double><<<grid_for(c, n), kThreads, 0, c->stream>>>(x, c->xb, c->perm, n);
+    }
+    EK_TRY(check_launch("k_scatter"));
+    EK_CUDA(cudaStreamSynchronize(c->stream));
+    EK_TRY(collect_profile(c));
+    if (iters) *iters = it;
+    if (hlen) *hlen = hl;
+    return status;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------------------
+// Exported entry points
+// ---------------------------------------------------------------------------------------
+extern "C" {
+
+void ekcg_default_opts(ekcg_opts* o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->variant = EKCG_SRE;
+    o->basis = EKCG_SSTEP;
+    o->orth = EKCG_ACHOLQR;
+    o->precision = EKCG_FP64;
+    o->max_s = 8;
+    o->max_blocks = 0;
+    o->max_basis_bytes = 0;
+    o->breakdown_tol = 1e-14;
+    o->inner_tol = 1e-4;
+    o->max_refine = 30;
+    o->profile = 0;
+}
+
+int ekcg_setup(int64_t n, const int64_t* rowptr, const int32_t* colind, const double* val,
+               int t, const int32_t* part, const ekcg_opts* opts, void* stream,
+               ekcg_ctx** out) {
+    if (!out) {
+        set_error("ekcg_setup", "out is NULL");
+        return EKCG_EINVAL;
+    }
+    *out = nullptr;
+    ekcg_ctx* c = new ekcg_ctx();
+    if (opts)
+        c->opts = *opts;
+    else
+        ekcg_default_opts(&c->opts);
+    const ekcg_opts& o = c->opts;
+    if (o.variant < 0 || o.variant > 2 || o.basis < 0 || o.basis > 2 || o.orth < 0 ||
+        o.orth > 1 || o.precision < 0 || o.precision > 1 || o.max_s < 1 ||
+        o.max_s * t > kPMax || o.max_blocks < 0 || !(o.breakdown_tol >= 0) ||
+        !(o.inner_tol > 0 && o.inner_tol < 1) || o.max_refine < 1) {
+        set_error("ekcg_setup", "invalid options (note: max_s * t must be <= 256)");
+        delete c;
+        return EKCG_EINVAL;
+    }
+    c->stream = (cudaStream_t)stream;
+    int rc = EKCG_OK;
+    cudaError_t e = cudaGetDevice(&c->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount,
+                                                     c->device);
+    if (e != cudaSuccess) {
+        set_error("ekcg_setup", cudaGetErrorString(e));
+        rc = EKCG_ECUDA;
+    }
+    if (rc == EKCG_OK) rc = validate_and_setup(n, rowptr, colind, val, t, part, c);
+    if (rc == EKCG_OK) rc = alloc_workspace(c);
+    if (rc != EKCG_OK) {
+        if (rc == EKCG_ECUDA && g_last_error.find("out of memory") != std::string::npos)
+            rc = EKCG_ENOMEM;
+        free_ctx(c);
+        delete c;
+        return rc;
+    }
+    *out = c;
+    return EKCG_OK;
+}
+
+int ekcg_solve(ekcg_ctx* c, const double* b, const double* x0, int s, double tol, int maxit,
+               double* x, int* iters, double* res_hist, int hist_cap, int* hist_len) {
+    if (!c || !b || !x || s < 1 || s > c->opts.max_s || !(tol > 0) || maxit < 0 ||
+        hist_cap < 0) {
+        set_error("ekcg_solve", "bad arguments");
+        return EKCG_EINVAL;
+    }
+    return solve_device(c, b, x0, s, tol, maxit, x, iters, res_hist, hist_cap, hist_len);
+}
+
+int ekcg_solve_host(ekcg_ctx* c, const double* b_host, const double* x0_host, int s, double tol,
+                    int maxit, double* x_host, int* iters, double* res_hist, int hist_cap,
+                    int* hist_len) {
+    if (!c || !b_host || !x_host) {
+        set_error("ekcg_solve_host", "bad arguments");
+        return EKCG_EINVAL;
+    }
+    const int64_t n = c->n;
+    double* db = c->nat_tmp;
+    double* dx = c->nat_tmp + n;
+    EK_CUDA(cudaMemcpyAsync(db, b_host, n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    if (x0_host)
+        EK_CUDA(cudaMemcpyAsync(dx, x0_host, n * sizeof(double), cudaMemcpyHostToDevice,
+                                c->stream));
+    int rc = ekcg_solve(c, db, x0_host ? dx : nullptr, s, tol, maxit, dx, iters, res_hist,
+                        hist_cap, hist_len);
+    if (rc < 0 && rc != EKCG_EBREAKDOWN && rc != EKCG_ENOMEM) return rc;
+    EK_CUDA(cudaMemcpyAsync(x_host, dx, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    EK_CUDA(cudaStreamSynchronize(c->stream));
+    return rc;
+}
+
+void ekcg_destroy(ekcg_ctx* c) {
+    if (!c) return;
+    free_ctx(c);
+    delete c;
+}
+
+const char* ekcg_strerror(int s) {
+    switch (s) {
+        case EKCG_OK: return "ok";
+        case EKCG_MAXIT: return "maximum iterations reached";
+        case EKCG_EINVAL: return "invalid argument";
+        case EKCG_ENOMEM: return "out of device memory or stored-basis capacity";
+        case EKCG_EBREAKDOWN: return "Cholesky breakdown in the A-orthonormalisation";
+        case EKCG_ETIMEOUT: return "device wait timed out";
+        case EKCG_ECUDA: return "CUDA runtime error";
+        default: return "unknown status";
+    }
+}
+
+const char* ekcg_last_error(void) { return g_last_error.c_str(); }
+
+int ekcg_shape(const ekcg_ctx* c, int64_t* n, int* t, int64_t* nnz) {
+    if (!c) return EKCG_EINVAL;
+    if (n) *n = c->n;
+    if (t) *t = c->t;
+    if (nnz) *nnz = c->nnz;
+    return EKCG_OK;
+}
+
+int ekcg_get_perm(const ekcg_ctx* c, int64_t* perm) {
+    if (!c || !perm) return EKCG_EINVAL;
+    std::memcpy(perm, c->perm_h.data(), c->n * sizeof(int64_t));
+    return EKCG_OK;
+}
+
+int ekcg_last_stats(const ekcg_ctx* c, int64_t* kl, int64_t* sp) {
+    if (!c) return EKCG_EINVAL;
+    if (kl) *kl = c->launches;
+    if (sp) *sp = c->spmm_calls;
+    return EKCG_OK;
+}
+
+int ekcg_profile(const ekcg_ctx* c, int cap, const char** names, double* ms, int64_t* launches,
+                 double* flops, double* bytes, int* count) {
+    if (!c || cap < 0) return EKCG_EINVAL;
+    int k = 0;
+    for (int i = 0; i < KC_COUNT; ++i) {
+        if (c->cls_n[i] == 0) continue;
+        if (k < cap) {
+            if (names) names[k] = kClassNames[i];
+            if (ms) ms[k] = c->prof_ms[i];
+            if (launches) launches[k] = c->cls_n[i];
+            if (flops) flops[k] = c->alg_flops[i];
+            if (bytes) bytes[k] = c->alg_bytes[i];
+        }
+        ++k;
+    }
+    if (count) *count = k;
+    return EKCG_OK;
+}
+
+int ekcg_split_T(ekcg_ctx* c, const double* r, double* T) {
+    if (!c || !r || !T) return EKCG_EINVAL;
+    EK_TRY(run_split<double>(c, r, T));
+    EK_CUDA(cudaStreamSynchronize(c->stream));
+    return EKCG_OK;
+}
+
+int ekcg_spmm(ekcg_ctx* c, const double* W, double* U, int w) {
+    if (!c || !W || !U || w < 1 || w > 256) return EKCG_EINVAL;
+    EK_TRY(run_spmm<double>(c, W, U, w));
+    EK_CUDA(cudaStreamSynchronize(c->stream));
+    return EKCG_OK;
+}
+
+int ekcg_update_values(ekcg_ctx* c, const double* val) {
+    if (!c || !val) return EKCG_EINVAL;
+    {
+        Launch L(c, KC_MISC);
+        k_refresh_values<<<grid_for(c, c->nnz), kThreads, 0, c->stream>>>(c->val, c->val32, val,
+                                                                         c->nzmap, c->nnz);
+    }
+    EK_TRY(check_launch("k_refresh_values"));
+    EK_CUDA(cudaStreamSynchronize(c->stream));
+    return EKCG_OK;
+}
+
+int ekcg_grad_A(ekcg_ctx* c, const double* lam, const double* x, double* dval) {
+    if (!c || !lam || !x || !dval) return EKCG_EINVAL;
+    {
+        Launch L(c, KC_MISC);
+        k_grad_A<<<grid_for(c, c->n), kThreads, 0, c->stream>>>(dval, lam, x, c->rowptr, c->col,
+                                                               c->perm, c->nzmap, c->n);
+    }
+    EK_TRY(check_launch("k_grad_A"));
+    EK_CUDA(cudaStreamSynchronize(c->stream));
+    return EKCG_OK;
+}
+
+int ekcg_diffusion2d_values(ekcg_ctx* c, int nx, int ny, double ax, double ay,
+                            const double* log_kappa, double* val) {
+    if (!c || !log_kappa || !val || nx < 1 || ny < 1 || (int64_t)nx * ny != c->n) {
+        set_error("ekcg_diffusion2d_values", "grid does not match the context");
+        return EKCG_EINVAL;
+    }
+    {
+        Launch L(c, KC_MISC);
+        k_diffusion2d_values<<<grid_for(c, c->n), kThreads, 0, c->stream>>>(
+            val, log_kappa, c->nat_rowptr, nx, ny, ax, ay);
+    }
+    EK_TRY(check_launch("k_diffusion2d_values"));
+    EK_CUDA(cudaStreamSynchronize(c->stream));
+    return EKCG_OK;
+}
+
+int ekcg_diffusion2d_grad_logkappa(ekcg_ctx* c, int nx, int ny, double ax, double ay,
+                                   const double* log_kappa, const double* lam, const double* x,
+                                   double* grad) {
+    if (!c || !log_kappa || !lam || !x || !grad || nx < 1 || ny < 1 ||
+        (int64_t)nx * ny != c->n) {
+        set_error("ekcg_diffusion2d_grad_logkappa", "grid does not match the context");
+        return EKCG_EINVAL;
+    }
+    {
+        Launch L(c, KC_MISC);
+        k_diffusion2d_grad_logk<<<grid_for(c, c->n), kThreads, 0, c->stream>>>(
+            grad, log_kappa, lam, x, nx, ny, ax, ay);
+    }
+    EK_TRY(check_launch("k_diffusion2d_grad_logk"));
+    EK_CUDA(cudaStreamSynchronize(c->stream));
+    return EKCG_OK;
+}
+
+int ekcg_permute(ekcg_ctx* c, const double* x, double* y, int direction) {
+    if (!c || !x || !y || (direction != 0 && direction != 1)) return EKCG_EINVAL;
+    if (direction == 0)
+        k_gather<double><<<grid_for(c, c->n), kThreads, 0, c->stream>>>(y, x, c->perm, c->n);
+    else
+        k_scatter<double><<<grid_for(c, c->n), kThreads, 0, c->stream>>>(y, x, c->perm, c->n);
+    EK_TRY(check_launch("permute"));
+    EK_CUDA(cudaStreamSynchronize(c->stream));
+    return EKCG_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,488 @@
+// Device kernels of the s-step enlarged CG path (sm_103a).
+//
+// Every n x w block of vectors is row-major (element (i, c) at [i*w + c]); a multi-block
+// operand (MB) is `count` such blocks kept in a ring of equally spaced slots, so the basis
+// window of s-step SRE-CG (Algorithm 4), the (s+1)t window of CA SRE-CG and the full history
+// of SRE-CG2 / MSDO-CG (Algorithms 3, 6) all use the same descriptor.
+//
+// Reductions over the n rows (block inner products, Gram matrices, residual norms) are
+// two-stage and deterministic: a fixed grid writes one partial per CTA, a second kernel sums
+// the partials in CTA order.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace ekcg {
+
+constexpr int kThreads = 256;
+constexpr int kGramRows = 32;   // rows staged per step of the Gram kernel
+constexpr int kGramTile = 64;   // output tile of the Gram kernel (kGramTile^2 per CTA)
+constexpr int kUpdRows = 32;    // rows per step of the block-update kernel
+constexpr int kPMax = 256;      // max contraction width of one block-update launch
+
+template <typename T>
+struct MB {
+    T* base;         // slot 0
+    int64_t stride;  // elements between consecutive slots
+    int first;       // slot holding block 0
+    int count;       // number of blocks
+    int ring;        // number of slots in the ring
+    int w;           // columns per block
+    __host__ __device__ __forceinline__ T* blk(int i) const {
+        return base + (int64_t)((first + i) % ring) * stride;
+    }
+    __host__ __device__ __forceinline__ int cols() const { return count * w; }
+};
+
+template <typename T>
+__host__ __device__ inline MB<const T> as_const(const MB<T>& m) {
+    return MB<const T>{m.base, m.stride, m.first, m.count, m.ring, m.w};
+}
+
+// Deterministic CTA-wide sum (fixed shuffle tree, then warp sums in warp order).
+template <typename Acc>
+__device__ __forceinline__ Acc block_sum(Acc v, Acc* red) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) red[wid] = v;
+    __syncthreads();
+    Acc s = 0;
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += red[i];
+    }
+    __syncthreads();
+    return s;
+}
+
+// ---------------------------------------------------------------------------------------
+// Permutations, splitting operator T (Section 2), residual
+// ---------------------------------------------------------------------------------------
+
+template <typename T>
+__global__ void k_gather(T* __restrict__ y, const T* __restrict__ x,
+                         const int32_t* __restrict__ perm, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        y[i] = x[perm[i]];
+}
+
+template <typename T>
+__global__ void k_scatter(T* __restrict__ y, const T* __restrict__ x,
+                          const int32_t* __restrict__ perm, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        y[perm[i]] = x[i];
+}
+
+// T(r): row i of the n x t block holds r_i in the column of its domain, zeros elsewhere.
+template <typename T>
+__global__ void k_split_T(T* __restrict__ out, const T* __restrict__ r,
+                          const int32_t* __restrict__ dom, int64_t n, int t) {
+    const int64_t total = n * t;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = e / t;
+        const int c = (int)(e - i * t);
+        out[e] = (c == dom[i]) ? r[i] : T(0);
+    }
+}
+
+// r = b - A x (float64) and per-CTA partials of ||r||^2.
+__global__ void k_residual(double* __restrict__ r, const double* __restrict__ b,
+                           const double* __restrict__ x, const int32_t* __restrict__ rowptr,
+                           const int32_t* __restrict__ col, const double* __restrict__ val,
+                           int64_t n, double* __restrict__ partials) {
+    __shared__ double red[32];
+    double local = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        double acc = 0.0;
+        for (int j = rowptr[i]; j < rowptr[i + 1]; ++j) acc += val[j] * x[col[j]];
+        const double ri = b[i] - acc;
+        r[i] = ri;
+        local += ri * ri;
+    }
+    const double s = block_sum(local, red);
+    if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
+// out = sqrt(sum of partials), summed in CTA order.
+__global__ void k_norm_finalize(const double* __restrict__ partials, int g,
+                                double* __restrict__ out) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        double s = 0.0;
+        for (int i = 0; i < g; ++i) s += partials[i];
+        out[0] = sqrt(s);
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// Sparse matrix x block of vectors: U = A W (CSR, one thread per output element)
+// ---------------------------------------------------------------------------------------
+
+template <typename T>
+__global__ void k_spmm(T* __restrict__ U, const T* __restrict__ W,
+                       const int32_t* __restrict__ rowptr, const int32_t* __restrict__ col,
+                       const T* __restrict__ val, int64_t n, int w) {
+    const int64_t total = n * w;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = e / w;
+        const int c = (int)(e - i * w);
+        T acc = T(0);
+        const int j1 = rowptr[i + 1];
+        for (int j = rowptr[i]; j < j1; ++j) acc += val[j] * W[(int64_t)col[j] * w + c];
+        U[e] = acc;
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// Tall-skinny products C = X^T Y (Gram matrices, CGS coefficients, alpha = V^T r)
+// ---------------------------------------------------------------------------------------
+
+// Stage rows [r0, r0 + kGramRows) x columns [c0, c0 + width) of a multi-block operand.
+template <typename T, typename Acc, int LD>
+__device__ __forceinline__ void stage_cols(Acc* dst, const MB<const T>& X, int64_t r0, int64_t n,
+                                           int c0, int width) {
+    const int P = X.cols();
+    for (int e = threadIdx.x; e < kGramRows * width; e += blockDim.x) {
+        const int rr = e / width, cc = e - rr * width;
+        const int64_t row = r0 + rr;
+        const int gc = c0 + cc;
+        Acc v = Acc(0);
+        if (row < n && gc < P) {
+            const int b = gc / X.w;
+            v = (Acc)X.blk(b)[row * X.w + (gc - b * X.w)];
+        }
+        dst[rr * LD + cc] = v;
+    }
+}
+
+// Output tile (TPT*MP) x (TQT*MQ); TPT*TQT = kThreads threads, each an MP x MQ micro-tile.
+// grid = (G row CTAs, tiles); partials[(tile*G + cta)*kGramTile^2 + i*TQ + j]
+// (each tile's partials keep a kGramTile^2 stride whatever the tile shape).
+template <typename T, typename Acc, int TPT, int TQT, int MP, int MQ>
+__global__ void __launch_bounds__(kThreads)
+k_gram_partial(MB<const T> X, MB<const T> Y, int64_t n, int ntq, Acc* __restrict__ partials) {
+    constexpr int TP = TPT * MP, TQ = TQT * MQ;
+    static_assert(TPT * TQT == kThreads, "thread layout");
+    static_assert(TP * TQ <= kGramTile * kGramTile, "tile");
+    __shared__ Acc xs[kGramRows * (TP + 1)];
+    __shared__ Acc ys[kGramRows * (TQ + 1)];
+    const int tile = blockIdx.y;
+    const int p0 = (tile / ntq) * TP, q0 = (tile % ntq) * TQ;
+    const int ti = threadIdx.x / TQT, tj = threadIdx.x % TQT;
+    Acc acc[MP][MQ];
+#pragma unroll
+    for (int a = 0; a < MP; ++a)
+#pragma unroll
+        for (int c = 0; c < MQ; ++c) acc[a][c] = Acc(0);
+    for (int64_t r0 = (int64_t)blockIdx.x * kGramRows; r0 < n;
+         r0 += (int64_t)gridDim.x * kGramRows) {
+        stage_cols<T, Acc, TP + 1>(xs, X, r0, n, p0, TP);
+        stage_cols<T, Acc, TQ + 1>(ys, Y, r0, n, q0, TQ);
+        __syncthreads();
+#pragma unroll 4
+        for (int rr = 0; rr < kGramRows; ++rr) {
+            Acc a[MP], bq[MQ];
+#pragma unroll
+            for (int k = 0; k < MP; ++k) a[k] = xs[rr * (TP + 1) + ti * MP + k];
+#pragma unroll
+            for (int k = 0; k < MQ; ++k) bq[k] = ys[rr * (TQ + 1) + tj * MQ + k];
+#pragma unroll
+            for (int k = 0; k < MP; ++k)
+#pragma unroll
+                for (int l = 0; l < MQ; ++l) acc[k][l] += a[k] * bq[l];
+        }
+        __syncthreads();
+    }
+    Acc* out = partials + ((int64_t)tile * gridDim.x + blockIdx.x) * (kGramTile * kGramTile);
+#pragma unroll
+    for (int k = 0; k < MP; ++k)
+#pragma unroll
+        for (int l = 0; l < MQ; ++l) out[(ti * MP + k) * TQ + tj * MQ + l] = acc[k][l];
+}
+
+// C[(c_row0 + p)*ldc + q] = sum over CTAs of the partials, p < P, q < Q.
+template <typename Acc, typename Out>
+__global__ void k_gram_reduce(const Acc* __restrict__ partials, int g, int ntq, int TP, int TQ,
+                              int P, int Q, Out* __restrict__ C, int ldc, int c_row0) {
+    const int total = P * Q;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
+        const int p = e / Q, q = e - p * Q;
+        const int tile = (p / TP) * ntq + q / TQ;
+        const int loc = (p % TP) * TQ + (q % TQ);
+        const Acc* src = partials + (int64_t)tile * g * (kGramTile * kGramTile) + loc;
+        Acc s = Acc(0);
+        for (int c = 0; c < g; ++c) s += src[(int64_t)c * (kGramTile * kGramTile)];
+        C[(int64_t)(c_row0 + p) * ldc + q] = (Out)s;
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// Block update: OUT = beta*Y + alpha * X C  (CGS step W - Q C, A W - (AQ) C, and W R^{-1})
+// ---------------------------------------------------------------------------------------
+// X has P <= kPMax columns; C is P x Q with leading dimension ldc starting at row c_row0.
+// upper = 1 when C is upper triangular (only k <= q contributes).  OUT may alias X or Y:
+// each CTA stages its rows of X in shared memory before writing any of them.
+template <typename T, typename CT>
+__global__ void __launch_bounds__(kThreads)
+k_update(MB<const T> X, const CT* __restrict__ C, int ldc, int c_row0, MB<const T> Y,
+         MB<T> OUT, int64_t n, int beta_on, CT alpha, int upper) {
+    extern __shared__ unsigned char smem_raw[];
+    T* xs = reinterpret_cast<T*>(smem_raw);
+    const int P = X.cols(), Q = OUT.cols();
+    const int ldx = P + 1;
+    for (int64_t r0 = (int64_t)blockIdx.x * kUpdRows; r0 < n;
+         r0 += (int64_t)gridDim.x * kUpdRows) {
+        for (int e = threadIdx.x; e < kUpdRows * P; e += blockDim.x) {
+            const int rr = e / P, cc = e - rr * P;
+            const int64_t row = r0 + rr;
+            const int b = cc / X.w;
+            xs[rr * ldx + cc] = (row < n) ? X.blk(b)[row * X.w + (cc - b * X.w)] : T(0);
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < kUpdRows * Q; e += blockDim.x) {
+            const int rr = e / Q, q = e - rr * Q;
+            const int64_t row = r0 + rr;
+            if (row < n) {
+                CT acc = CT(0);
+                const int kend = upper ? min(P, q + 1) : P;
+                const T* xr = xs + rr * ldx;
+                const CT* cp = C + (int64_t)c_row0 * ldc + q;
+                for (int k = 0; k < kend; ++k) acc += (CT)xr[k] * cp[(int64_t)k * ldc];
+                const int bo = q / OUT.w, co = q - bo * OUT.w;
+                CT y = CT(0);
+                if (beta_on) {
+                    const int by = q / Y.w;
+                    y = (CT)Y.blk(by)[row * Y.w + (q - by * Y.w)];
+                }
+                OUT.blk(bo)[row * OUT.w + co] = (T)(y + alpha * acc);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// Small dense Cholesky G = R^T R (upper, from the upper triangle of G) and R^{-1}
+// ---------------------------------------------------------------------------------------
+// One CTA.  Right-looking, same operation order as the oracle.  Breakdown rule:
+// d_i <= tol*|G_ii| or non-finite sets bit 0 of *flag and leaves R = Rinv = I.
+__global__ void k_chol_inv(const double* __restrict__ G, int m, double* __restrict__ S,
+                           double* __restrict__ R, double* __restrict__ Rinv, double tol,
+                           int* __restrict__ flag) {
+    __shared__ int bad;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    for (int e = tid; e < m * m; e += nt) {
+        const int i = e / m, j = e - i * m;
+        S[e] = (j >= i) ? G[e] : 0.0;
+        R[e] = 0.0;
+        Rinv[e] = 0.0;
+    }
+    if (tid == 0) bad = (*flag) & 1;
+    __syncthreads();
+    for (int i = 0; i < m && !bad; ++i) {
+        if (tid == 0) {
+            const double d = S[i * m + i];
+            if (!(d > tol * fabs(G[i * m + i])) || !isfinite(d))
+                bad = 1;
+            else
+                R[i * m + i] = sqrt(d);
+        }
+        __syncthreads();
+        if (bad) break;
+        const double rii = R[i * m + i];
+        for (int j = i + 1 + tid; j < m; j += nt) R[i * m + j] = S[i * m + j] / rii;
+        __syncthreads();
+        const int rem = m - i - 1;
+        for (int e = tid; e < rem * rem; e += nt) {
+            const int j = i + 1 + e / rem, l = i + 1 + e % rem;
+            if (l >= j) S[j * m + l] -= R[i * m + j] * R[i * m + l];
+        }
+        __syncthreads();
+    }
+    if (bad) {
+        for (int e = tid; e < m * m; e += nt) {
+            const int i = e / m, j = e - i * m;
+            R[e] = (i == j) ? 1.0 : 0.0;
+            Rinv[e] = R[e];
+        }
+        if (tid == 0) atomicOr(flag, 1);
+        return;
+    }
+    // R^{-1} by back substitution, one column per thread.
+    for (int c = tid; c < m; c += nt) {
+        for (int i = c; i >= 0; --i) {
+            double s = (i == c) ? 1.0 : 0.0;
+            for (int k = i + 1; k <= c; ++k) s -= R[i * m + k] * Rinv[k * m + c];
+            Rinv[i * m + c] = s / R[i * m + i];
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// x += V alpha, r -= (A V) alpha, partials of ||r||^2   (Algorithm 4 last three lines)
+// ---------------------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+k_xr_update(T* __restrict__ x, T* __restrict__ r, MB<const T> V, MB<const T> Z,
+            const double* __restrict__ alpha, int64_t n, double* __restrict__ partials,
+            const int* __restrict__ flag) {
+    __shared__ double red[32];
+    const bool skip = (*flag) != 0;   // breakdown: keep the last complete iterate
+    double local = 0.0;
+    if (!skip) {
+        const int w = V.w;
+        for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+             i += (int64_t)gridDim.x * blockDim.x) {
+            double sx = 0.0, sr = 0.0;
+            for (int b = 0; b < V.count; ++b) {
+                const T* vb = V.blk(b) + i * w;
+                const T* zb = Z.blk(b) + i * w;
+                const double* ab = alpha + b * w;
+                for (int c = 0; c < w; ++c) {
+                    sx += (double)vb[c] * ab[c];
+                    sr += (double)zb[c] * ab[c];
+                }
+            }
+            const T xi = (T)((double)x[i] + sx);
+            const T ri = (T)((double)r[i] - sr);
+            x[i] = xi;
+            r[i] = ri;
+            local += (double)ri * (double)ri;
+        }
+    }
+    const double s = block_sum(local, red);
+    if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
+// ---------------------------------------------------------------------------------------
+// Mixed precision helpers (float64 <-> float32 with scaling)
+// ---------------------------------------------------------------------------------------
+__global__ void k_to_float_scaled(float* __restrict__ y, const double* __restrict__ x,
+                                  const double* __restrict__ norm, int64_t n) {
+    const double sc = norm[0] > 0.0 ? 1.0 / norm[0] : 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        y[i] = (float)(x[i] * sc);
+}
+
+__global__ void k_axpy_scaled(double* __restrict__ x, const float* __restrict__ d,
+                              const double* __restrict__ norm, int64_t n) {
+    const double sc = norm[0];
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        x[i] += sc * (double)d[i];
+}
+
+// ---------------------------------------------------------------------------------------
+// Matrix values on a fixed pattern, adjoint gradients, 2D diffusion model (edge form)
+// ---------------------------------------------------------------------------------------
+
+// val[jp] = vnat[map[jp]] (permuted storage from the caller's natural CSR order).
+__global__ void k_refresh_values(double* __restrict__ val, float* __restrict__ val32,
+                                 const double* __restrict__ vnat, const int32_t* __restrict__ map,
+                                 int64_t nnz) {
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < nnz;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        const double v = vnat[map[j]];
+        val[j] = v;
+        val32[j] = (float)v;
+    }
+}
+
+// dL/dA_ij = -lambda_i x_j on the sparsity pattern, written in the caller's CSR order.
+// lambda and x are natural-order vectors.
+__global__ void k_grad_A(double* __restrict__ dval, const double* __restrict__ lam,
+                         const double* __restrict__ x, const int32_t* __restrict__ rowptr,
+                         const int32_t* __restrict__ col, const int32_t* __restrict__ perm,
+                         const int32_t* __restrict__ map, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const double li = lam[perm[i]];
+        for (int j = rowptr[i]; j < rowptr[i + 1]; ++j)
+            dval[map[j]] = -li * x[perm[col[j]]];
+    }
+}
+
+// Edge weight a * 2 k_p k_q / (k_p + k_q) (harmonic mean), no contraction so that the
+// value matches a plain evaluation of the same expression.
+__device__ __forceinline__ double hm_weight(double a, double kp, double kq) {
+    return __dmul_rn(a, __ddiv_rn(__dmul_rn(__dmul_rn(2.0, kp), kq), __dadd_rn(kp, kq)));
+}
+
+// Values of the 5-point edge-form diffusion matrix A(kappa), kappa = exp(log_kappa), in
+// natural CSR order with sorted columns (node p = i + nx*j).  Diagonal = sum of the edge
+// weights of p plus a*kappa_p per Dirichlet face, added x-axis first then y-axis.
+__global__ void k_diffusion2d_values(double* __restrict__ val, const double* __restrict__ logk,
+                                     const int32_t* __restrict__ rowptr, int nx, int ny,
+                                     double ax, double ay) {
+    const int64_t n = (int64_t)nx * ny;
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(p % nx), j = (int)(p / nx);
+        const double kp = exp(logk[p]);
+        double wxl = 0.0, wxr = 0.0, wyd = 0.0, wyu = 0.0;
+        if (i > 0) wxl = hm_weight(ax, exp(logk[p - 1]), kp);
+        if (i < nx - 1) wxr = hm_weight(ax, kp, exp(logk[p + 1]));
+        if (j > 0) wyd = hm_weight(ay, exp(logk[p - nx]), kp);
+        if (j < ny - 1) wyu = hm_weight(ay, kp, exp(logk[p + nx]));
+        double d = 0.0;
+        d = __dadd_rn(d, wxr);
+        d = __dadd_rn(d, wxl);
+        if (i == 0) d = __dadd_rn(d, __dmul_rn(ax, kp));
+        if (i == nx - 1) d = __dadd_rn(d, __dmul_rn(ax, kp));
+        d = __dadd_rn(d, wyu);
+        d = __dadd_rn(d, wyd);
+        if (j == 0) d = __dadd_rn(d, __dmul_rn(ay, kp));
+        if (j == ny - 1) d = __dadd_rn(d, __dmul_rn(ay, kp));
+        int o = rowptr[p];
+        if (j > 0) val[o++] = -wyd;
+        if (i > 0) val[o++] = -wxl;
+        val[o++] = d;
+        if (i < nx - 1) val[o++] = -wxr;
+        if (j < ny - 1) val[o++] = -wyu;
+    }
+}
+
+// dL/dlog(kappa_p) for L(x(kappa)), x = A(kappa)^{-1} b, lambda = A^{-1} dL/dx:
+// dL/dw_e = -(lambda_p - lambda_q)(x_p - x_q) for an edge, -lambda_p x_p for a face;
+// dw_e/dk_p = a * 2 k_q^2 / (k_p + k_q)^2, dw_face/dk_p = a; dk_p/dlog k_p = k_p.
+__global__ void k_diffusion2d_grad_logk(double* __restrict__ g, const double* __restrict__ logk,
+                                        const double* __restrict__ lam,
+                                        const double* __restrict__ x, int nx, int ny, double ax,
+                                        double ay) {
+    const int64_t n = (int64_t)nx * ny;
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < n;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(p % nx), j = (int)(p / nx);
+        const double kp = exp(logk[p]);
+        const double lp = lam[p], xp = x[p];
+        double acc = 0.0;
+        const int64_t nb[4] = {p - 1, p + 1, p - nx, p + nx};
+        const bool ok[4] = {i > 0, i < nx - 1, j > 0, j < ny - 1};
+        const double a[4] = {ax, ax, ay, ay};
+        for (int e = 0; e < 4; ++e) {
+            if (ok[e]) {
+                const int64_t q = nb[e];
+                const double kq = exp(logk[q]);
+                const double s = kp + kq;
+                acc += a[e] * (2.0 * kq * kq / (s * s)) * (-(lp - lam[q]) * (xp - x[q]));
+            } else {
+                acc += a[e] * (-lp * xp);
+            }
+        }
+        g[p] = kp * acc;
+    }
+}
+
+template <typename T>
+__global__ void k_fill(T* __restrict__ y, T v, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        y[i] = v;
+}
+
+}  // namespace ekcg

@@ -1,0 +1,300 @@
+"""Thin Python binding of libekcg (the C ABI declared in include/ekcg.h).
+
+Only argument marshalling lives here: every step of the solve runs in the library's CUDA
+kernels.  Device buffers are torch CUDA tensors (torch is used for memory and streams only).
+Importing this module does not need a GPU; calling into the library without the built
+library raises immediately (there is no CPU fallback).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+from ctypes import POINTER, byref, c_char_p, c_double, c_int, c_int64, c_void_p
+from typing import Optional
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "lib", "libekcg.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "ekcg.h")
+
+EKCG_OK, EKCG_MAXIT, EKCG_EINVAL, EKCG_ENOMEM, EKCG_EBREAKDOWN, EKCG_ETIMEOUT, EKCG_ECUDA = \
+    0, 1, -1, -2, -3, -4, -5
+VARIANT = {"sre": 0, "sre2": 1, "msdo": 2}
+BASIS = {"sstep": 0, "ca5": 1, "ca7": 2}
+ORTH = {"acholqr": 0, "precholqr": 1}
+PRECISION = {"fp64": 0, "fp32_ir": 1}
+
+
+class ekcg_opts(ctypes.Structure):
+    _fields_ = [("variant", c_int), ("basis", c_int), ("orth", c_int), ("precision", c_int),
+                ("max_s", c_int), ("max_blocks", c_int), ("max_basis_bytes", c_int64),
+                ("breakdown_tol", c_double), ("inner_tol", c_double), ("max_refine", c_int),
+                ("profile", c_int)]
+
+
+class EkcgError(RuntimeError):
+    def __init__(self, status, where=""):
+        self.status = status
+        super().__init__(f"{where}: {strerror(status)} ({status}): {last_error()}")
+
+
+_lib = None
+
+
+def _declare(L):
+    L.ekcg_default_opts.argtypes = [POINTER(ekcg_opts)]
+    L.ekcg_default_opts.restype = None
+    L.ekcg_setup.argtypes = [c_int64, c_void_p, c_void_p, c_void_p, c_int, c_void_p,
+                             POINTER(ekcg_opts), c_void_p, POINTER(c_void_p)]
+    L.ekcg_setup.restype = c_int
+    solve_args = [c_void_p, c_void_p, c_void_p, c_int, c_double, c_int, c_void_p,
+                  POINTER(c_int), c_void_p, c_int, POINTER(c_int)]
+    L.ekcg_solve.argtypes = solve_args
+    L.ekcg_solve.restype = c_int
+    L.ekcg_solve_host.argtypes = solve_args
+    L.ekcg_solve_host.restype = c_int
+    L.ekcg_destroy.argtypes = [c_void_p]
+    L.ekcg_destroy.restype = None
+    L.ekcg_strerror.argtypes = [c_int]
+    L.ekcg_strerror.restype = c_char_p
+    L.ekcg_last_error.argtypes = []
+    L.ekcg_last_error.restype = c_char_p
+    L.ekcg_shape.argtypes = [c_void_p, POINTER(c_int64), POINTER(c_int), POINTER(c_int64)]
+    L.ekcg_shape.restype = c_int
+    L.ekcg_get_perm.argtypes = [c_void_p, c_void_p]
+    L.ekcg_get_perm.restype = c_int
+    L.ekcg_last_stats.argtypes = [c_void_p, POINTER(c_int64), POINTER(c_int64)]
+    L.ekcg_last_stats.restype = c_int
+    L.ekcg_profile.argtypes = [c_void_p, c_int, POINTER(c_char_p), POINTER(c_double),
+                               POINTER(c_int64), POINTER(c_double), POINTER(c_double),
+                               POINTER(c_int)]
+    L.ekcg_profile.restype = c_int
+    L.ekcg_split_T.argtypes = [c_void_p, c_void_p, c_void_p]
+    L.ekcg_split_T.restype = c_int
+    L.ekcg_spmm.argtypes = [c_void_p, c_void_p, c_void_p, c_int]
+    L.ekcg_spmm.restype = c_int
+    L.ekcg_permute.argtypes = [c_void_p, c_void_p, c_void_p, c_int]
+    L.ekcg_permute.restype = c_int
+    L.ekcg_update_values.argtypes = [c_void_p, c_void_p]
+    L.ekcg_update_values.restype = c_int
+    L.ekcg_grad_A.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p]
+    L.ekcg_grad_A.restype = c_int
+    L.ekcg_diffusion2d_values.argtypes = [c_void_p, c_int, c_int, c_double, c_double, c_void_p,
+                                          c_void_p]
+    L.ekcg_diffusion2d_values.restype = c_int
+    L.ekcg_diffusion2d_grad_logkappa.argtypes = [c_void_p, c_int, c_int, c_double, c_double,
+                                                 c_void_p, c_void_p, c_void_p, c_void_p]
+    L.ekcg_diffusion2d_grad_logkappa.restype = c_int
+
+
+def lib():
+    """Load libekcg.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                               "`python -m paper_1804_10629_gb300.build`")
+        L = ctypes.CDLL(LIB_PATH)
+        _declare(L)
+        _lib = L
+    return _lib
+
+
+def header_functions():
+    """Names of the functions declared in include/ekcg.h."""
+    txt = open(HEADER).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(ekcg_\w+)\s*\(", txt)))
+
+
+def strerror(status: int) -> str:
+    return lib().ekcg_strerror(status).decode()
+
+
+def last_error() -> str:
+    return lib().ekcg_last_error().decode()
+
+
+def ekcg_default_opts() -> ekcg_opts:
+    o = ekcg_opts()
+    lib().ekcg_default_opts(byref(o))
+    return o
+
+
+def _ptr(a) -> int:
+    if hasattr(a, "data_ptr"):
+        return a.data_ptr()
+    return a.ctypes.data
+
+
+def ekcg_setup(n, rowptr, colind, val, t, part, opts=None, stream=None):
+    """Host numpy arrays in; returns an opaque context handle (int)."""
+    rowptr = np.ascontiguousarray(rowptr, dtype=np.int64)
+    colind = np.ascontiguousarray(colind, dtype=np.int32)
+    val = np.ascontiguousarray(val, dtype=np.float64)
+    part = np.ascontiguousarray(part, dtype=np.int32)
+    h = c_void_p()
+    st = lib().ekcg_setup(int(n), _ptr(rowptr), _ptr(colind), _ptr(val), int(t), _ptr(part),
+                          byref(opts) if opts is not None else None,
+                          c_void_p(stream) if stream else None, byref(h))
+    if st != EKCG_OK:
+        raise EkcgError(st, "ekcg_setup")
+    return h.value
+
+
+def ekcg_solve(ctx, b, x0, s, tol, maxit, x, hist_cap=0):
+    """Device pointers (torch tensors) b, x0 (or None), x.  Returns (status, iters, hist)."""
+    it = c_int(0)
+    hl = c_int(0)
+    hist = np.zeros(max(hist_cap, 1), dtype=np.float64)
+    st = lib().ekcg_solve(ctx, _ptr(b), _ptr(x0) if x0 is not None else None, int(s),
+                          float(tol), int(maxit), _ptr(x), byref(it), _ptr(hist),
+                          int(hist_cap), byref(hl))
+    return st, it.value, hist[:min(hl.value, hist_cap)]
+
+
+def ekcg_solve_host(ctx, b, x0, s, tol, maxit, x, hist_cap=0):
+    """Host numpy arrays b, x0 (or None), x (written).  Returns (status, iters, hist)."""
+    it = c_int(0)
+    hl = c_int(0)
+    hist = np.zeros(max(hist_cap, 1), dtype=np.float64)
+    st = lib().ekcg_solve_host(ctx, _ptr(b), _ptr(x0) if x0 is not None else None, int(s),
+                               float(tol), int(maxit), _ptr(x), byref(it), _ptr(hist),
+                               int(hist_cap), byref(hl))
+    return st, it.value, hist[:min(hl.value, hist_cap)]
+
+
+def ekcg_destroy(ctx):
+    if ctx:
+        lib().ekcg_destroy(ctx)
+
+
+def ekcg_shape(ctx):
+    n, t, nnz = c_int64(), c_int(), c_int64()
+    lib().ekcg_shape(ctx, byref(n), byref(t), byref(nnz))
+    return n.value, t.value, nnz.value
+
+
+def ekcg_get_perm(ctx, n):
+    p = np.empty(n, dtype=np.int64)
+    st = lib().ekcg_get_perm(ctx, _ptr(p))
+    if st != EKCG_OK:
+        raise EkcgError(st, "ekcg_get_perm")
+    return p
+
+
+def ekcg_last_stats(ctx):
+    kl, sp = c_int64(), c_int64()
+    lib().ekcg_last_stats(ctx, byref(kl), byref(sp))
+    return kl.value, sp.value
+
+
+def ekcg_profile(ctx, cap=32):
+    """{class: {"ms", "launches", "flops", "bytes"}} of the last solve."""
+    names = (c_char_p * cap)()
+    ms = (c_double * cap)()
+    nl = (c_int64 * cap)()
+    fl = (c_double * cap)()
+    by = (c_double * cap)()
+    cnt = c_int()
+    lib().ekcg_profile(ctx, cap, names, ms, nl, fl, by, byref(cnt))
+    return {names[i].decode(): {"ms": ms[i], "launches": nl[i], "flops": fl[i], "bytes": by[i]}
+            for i in range(min(cnt.value, cap))}
+
+
+def _check(st, where):
+    if st != EKCG_OK:
+        raise EkcgError(st, where)
+
+
+def ekcg_split_T(ctx, r, T):
+    _check(lib().ekcg_split_T(ctx, _ptr(r), _ptr(T)), "ekcg_split_T")
+
+
+def ekcg_spmm(ctx, W, U, w):
+    _check(lib().ekcg_spmm(ctx, _ptr(W), _ptr(U), int(w)), "ekcg_spmm")
+
+
+def ekcg_permute(ctx, x, y, direction):
+    _check(lib().ekcg_permute(ctx, _ptr(x), _ptr(y), int(direction)), "ekcg_permute")
+
+
+def ekcg_update_values(ctx, val):
+    _check(lib().ekcg_update_values(ctx, _ptr(val)), "ekcg_update_values")
+
+
+def ekcg_grad_A(ctx, lam, x, dval):
+    _check(lib().ekcg_grad_A(ctx, _ptr(lam), _ptr(x), _ptr(dval)), "ekcg_grad_A")
+
+
+def ekcg_diffusion2d_values(ctx, nx, ny, ax, ay, log_kappa, val):
+    _check(lib().ekcg_diffusion2d_values(ctx, int(nx), int(ny), float(ax), float(ay),
+                                         _ptr(log_kappa), _ptr(val)), "ekcg_diffusion2d_values")
+
+
+def ekcg_diffusion2d_grad_logkappa(ctx, nx, ny, ax, ay, log_kappa, lam, x, grad):
+    _check(lib().ekcg_diffusion2d_grad_logkappa(ctx, int(nx), int(ny), float(ax), float(ay),
+                                                _ptr(log_kappa), _ptr(lam), _ptr(x),
+                                                _ptr(grad)), "ekcg_diffusion2d_grad_logkappa")
+
+
+class Solver:
+    """Convenience wrapper owning one context (device work on the current torch stream)."""
+
+    def __init__(self, A, t, part, variant="sre", basis="sstep", orth="acholqr",
+                 precision="fp64", max_s=8, max_blocks=0, max_basis_bytes=0,
+                 breakdown_tol=1e-14, inner_tol=1e-4, max_refine=30, profile=False,
+                 stream=None):
+        import torch
+        o = ekcg_default_opts()
+        o.variant, o.basis, o.orth = VARIANT[variant], BASIS[basis], ORTH[orth]
+        o.precision = PRECISION[precision]
+        o.max_s, o.max_blocks, o.max_basis_bytes = max_s, max_blocks, max_basis_bytes
+        o.breakdown_tol, o.inner_tol, o.max_refine = breakdown_tol, inner_tol, max_refine
+        o.profile = int(bool(profile))
+        if stream is None:
+            stream = torch.cuda.current_stream().cuda_stream
+        self.n = int(A.n)
+        self.nnz = int(A.rowptr[-1])
+        self.t = int(t)
+        self.ctx = ekcg_setup(A.n, A.rowptr, A.colind, A.val, t, part, o, stream)
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            ekcg_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def solve(self, b, x0=None, s=2, tol=1e-8, maxit=1000, hist_cap=4096, x=None):
+        import torch
+        if x is None:
+            x = torch.empty_like(b)
+        st, it, hist = ekcg_solve(self.ctx, b, x0, s, tol, maxit, x, hist_cap)
+        if st < 0 and st not in (EKCG_EBREAKDOWN, EKCG_ENOMEM):
+            raise EkcgError(st, "ekcg_solve")
+        return x, it, hist, st
+
+    def solve_host(self, b, x0=None, s=2, tol=1e-8, maxit=1000, hist_cap=4096):
+        x = np.empty(self.n, dtype=np.float64)
+        st, it, hist = ekcg_solve_host(self.ctx, np.ascontiguousarray(b, dtype=np.float64),
+                                       None if x0 is None else np.ascontiguousarray(x0),
+                                       s, tol, maxit, x, hist_cap)
+        if st < 0 and st not in (EKCG_EBREAKDOWN, EKCG_ENOMEM):
+            raise EkcgError(st, "ekcg_solve_host")
+        return x, it, hist, st
+
+    def perm(self):
+        return ekcg_get_perm(self.ctx, self.n)
+
+    def stats(self):
+        return ekcg_last_stats(self.ctx)
+
+    def profile(self):
+        return ekcg_profile(self.ctx)
