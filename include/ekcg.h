@@ -179,6 +179,44 @@ int ekcg_diffusion2d_grad_logkappa(ekcg_ctx* ctx, int nx, int ny, double ax, dou
 /* y[i] = x[perm[i]] (direction 0: natural -> permuted) or y[perm[i]] = x[i] (direction 1).*/
 int ekcg_permute(ekcg_ctx* ctx, const double* x, double* y, int direction);
 
+/* ---- batched solves: many independent systems in one persistent launch ----------- */
+/* Not in the paper: the s-step SRE-CG of Algorithm 4 (A-CholQR, fresh-product CGS2) run on
+ * nsys independent SPD systems at once.  One CTA solves one system at a time, taking
+ * systems from a device queue, largest first; the gather, the solve and the scatter are one
+ * captured CUDA graph replayed per call.                                                   */
+typedef struct ekcg_batch ekcg_batch;
+
+/* n[nsys]: system sizes.  rowptr: the nsys local row-pointer arrays (n_k + 1 entries each,
+ * starting at 0) concatenated; colind (local column indices) and val: the nsys nonzero
+ * arrays concatenated; part: the nsys partitions (local domain ids in [0, t)) concatenated.
+ * All host arrays, copied.  t <= 16; opts: variant SRE, basis SSTEP, orth ACHOLQR, max_s <= 4,
+ * precision FP64 or FP32_IR (inner_tol, max_refine, breakdown_tol apply).
+ * Errors: EKCG_EINVAL, EKCG_ENOMEM, EKCG_ECUDA.                                           */
+int ekcg_batched_setup(int nsys, const int64_t* n, const int64_t* rowptr, const int32_t* colind,
+                       const double* val, int t, const int32_t* part, const ekcg_opts* opts,
+                       void* stream, ekcg_batch** out);
+
+/* Solve all systems with x0 = 0: b and x are device arrays of sum(n) doubles (the systems'
+ * vectors concatenated, natural order).  iters[nsys] and status[nsys] (host, nullable)
+ * receive each system's s-step iteration count (FP32_IR: inner iterations) and status
+ * (EKCG_OK, EKCG_MAXIT, EKCG_EBREAKDOWN, EKCG_EINVAL for a non-finite right-hand side).
+ * The call returns EKCG_OK when the launch ran; per-system outcomes are in status.        */
+int ekcg_batched_solve(ekcg_batch* batch, const double* b, int s, double tol, int maxit,
+                       double* x, int* iters, int* status);
+
+/* Time three launch shapes (threads per CTA x CTAs per SM) on right-hand side b and keep
+ * the fastest for later solves.                                                          */
+int ekcg_batched_tune(ekcg_batch* batch, const double* b, int s, double tol, int maxit);
+
+/* Launch shape in use and device time (ms) of the last captured solve.                   */
+int ekcg_batched_info(const ekcg_batch* batch, int* threads, int* ctas_per_sm, double* last_ms);
+
+/* Release the batch and its device memory (NULL accepted).                               */
+void ekcg_batched_destroy(ekcg_batch* batch);
+
+/* Text of the last batched-entry error seen by the calling thread.                        */
+const char* ekcg_batched_last_error(void);
+
 #ifdef __cplusplus
 }
 #endif

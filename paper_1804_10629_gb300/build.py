@@ -9,7 +9,7 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "lib", "libekcg.so")
-SOURCES = ["ekcg_api.cu"]
+SOURCES = ["ekcg_api.cu", "batched.cu"]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 
@@ -21,10 +21,23 @@ def nvcc():
 
 
 def build(verbose: bool = False, extra=()) -> str:
+    """Compile each translation unit in parallel, then link the shared library."""
     os.makedirs(os.path.dirname(LIB), exist_ok=True)
-    srcs = [os.path.join(CSRC, s) for s in SOURCES]
-    cmd = [nvcc(), "-O3", ARCH, "-lineinfo", "-std=c++17", "-shared", "-Xcompiler", "-fPIC",
-           "-o", LIB + ".tmp", *srcs, *extra]
+    objdir = os.path.join(HERE, "lib", "obj")
+    os.makedirs(objdir, exist_ok=True)
+    procs, objs = [], []
+    for src in SOURCES:
+        obj = os.path.join(objdir, src.replace(".cu", ".o"))
+        cmd = [nvcc(), "-O3", ARCH, "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
+               "-c", os.path.join(CSRC, src), "-o", obj, *extra]
+        if verbose:
+            print(" ".join(cmd), flush=True)
+        procs.append(subprocess.Popen(cmd))
+        objs.append(obj)
+    for p in procs:
+        if p.wait() != 0:
+            raise RuntimeError("nvcc failed")
+    cmd = [nvcc(), ARCH, "-shared", "-o", LIB + ".tmp", *objs]
     if verbose:
         print(" ".join(cmd), flush=True)
     subprocess.run(cmd, check=True)

@@ -239,28 +239,36 @@ template <typename T, typename Acc, typename Out>
 int run_gram_chunk(ekcg_ctx* c, MB<const T> X, MB<const T> Y, Out* C, int ldc, int c_row0,
                    Acc* partials) {
     const int P = X.cols(), Q = Y.cols();
+    // tile (TPT*MP) x (TQT*MQ) chosen from P and Q so that no FMA is spent on padding
     int ntq = 1, TP = 64, TQ = 64;
     if (Q > 32) {
         EK_TRY((gram_shape<T, Acc, 16, 16, 4, 4>(c, X, Y, partials, &ntq)));
     } else if (Q > 16) {
         TQ = 32;
-        EK_TRY((gram_shape<T, Acc, 32, 8, 2, 4>(c, X, Y, partials, &ntq)));
+        if (P <= 32) {
+            TP = 32;
+            EK_TRY((gram_shape<T, Acc, 16, 16, 2, 2>(c, X, Y, partials, &ntq)));
+        } else {
+            EK_TRY((gram_shape<T, Acc, 32, 8, 2, 4>(c, X, Y, partials, &ntq)));
+        }
     } else if (Q > 4) {
         TQ = 16;
-        EK_TRY((gram_shape<T, Acc, 64, 4, 1, 4>(c, X, Y, partials, &ntq)));
+        if (P <= 16) {
+            TP = 16;
+            EK_TRY((gram_shape<T, Acc, 16, 16, 1, 1>(c, X, Y, partials, &ntq)));
+        } else if (P <= 32) {
+            TP = 32;
+            EK_TRY((gram_shape<T, Acc, 32, 8, 1, 2>(c, X, Y, partials, &ntq)));
+        } else {
+            EK_TRY((gram_shape<T, Acc, 64, 4, 1, 4>(c, X, Y, partials, &ntq)));
+        }
     } else if (Q > 1) {
         TQ = 4;
         EK_TRY((gram_shape<T, Acc, 64, 4, 1, 1>(c, X, Y, partials, &ntq)));
     } else {
-        TP = 64;
         TQ = 1;
-        if (P > 64) {
-            TP = 256;
-            EK_TRY((gram_shape<T, Acc, 256, 1, 1, 1>(c, X, Y, partials, &ntq)));
-        } else {
-            EK_TRY((gram_shape<T, Acc, 64, 4, 1, 1>(c, X, Y, partials, &ntq)));
-            TQ = 4;
-        }
+        TP = 256;
+        EK_TRY((gram_shape<T, Acc, 256, 1, 1, 1>(c, X, Y, partials, &ntq)));
     }
     EK_TRY(check_launch("k_gram_partial"));
     const int g = c->grid_rows;

@@ -141,6 +141,41 @@ __global__ void k_spmm(T* __restrict__ U, const T* __restrict__ W,
 // Tall-skinny products C = X^T Y (Gram matrices, CGS coefficients, alpha = V^T r)
 // ---------------------------------------------------------------------------------------
 
+// Float-float accumulator: hi + lo carries about 48 significant bits.  add_prod adds the
+// exact product a*b (the rounding error of the float product is recovered with an FMA)
+// using TwoSum on the high part.
+struct DF {
+    float hi, lo;
+};
+__device__ __forceinline__ void df_add_prod(DF& acc, float a, float b) {
+    const float p = a * b;
+    const float e = fmaf(a, b, -p);
+    const float s = acc.hi + p;
+    const float v = s - acc.hi;
+    const float err = (acc.hi - (s - v)) + (p - v);
+    acc.hi = s;
+    acc.lo += err + e;
+}
+
+// Accumulation policy of the Gram kernel: Acc = T (plain), double from float64 data, and
+// float-float (stored as double) when float32 data must give a float64-grade Gram matrix.
+template <typename T, typename Acc>
+struct GramAcc {
+    using R = Acc;
+    __device__ __forceinline__ static void zero(R& a) { a = R(0); }
+    __device__ __forceinline__ static void add(R& a, T x, T y) { a += (R)x * (R)y; }
+    __device__ __forceinline__ static Acc out(const R& a) { return a; }
+};
+template <>
+struct GramAcc<float, double> {
+    using R = DF;
+    __device__ __forceinline__ static void zero(R& a) { a.hi = 0.f; a.lo = 0.f; }
+    __device__ __forceinline__ static void add(R& a, float x, float y) { df_add_prod(a, x, y); }
+    __device__ __forceinline__ static double out(const R& a) {
+        return (double)a.hi + (double)a.lo;
+    }
+};
+
 // Stage rows [r0, r0 + kGramRows) x columns [c0, c0 + width) of a multi-block operand.
 template <typename T, typename Acc, int LD>
 __device__ __forceinline__ void stage_cols(Acc* dst, const MB<const T>& X, int64_t r0, int64_t n,
@@ -168,24 +203,25 @@ k_gram_partial(MB<const T> X, MB<const T> Y, int64_t n, int ntq, Acc* __restrict
     constexpr int TP = TPT * MP, TQ = TQT * MQ;
     static_assert(TPT * TQT == kThreads, "thread layout");
     static_assert(TP * TQ <= kGramTile * kGramTile, "tile");
-    __shared__ Acc xs[kGramRows * (TP + 1)];
-    __shared__ Acc ys[kGramRows * (TQ + 1)];
+    using Pol = GramAcc<T, Acc>;
+    __shared__ T xs[kGramRows * (TP + 1)];
+    __shared__ T ys[kGramRows * (TQ + 1)];
     const int tile = blockIdx.y;
     const int p0 = (tile / ntq) * TP, q0 = (tile % ntq) * TQ;
     const int ti = threadIdx.x / TQT, tj = threadIdx.x % TQT;
-    Acc acc[MP][MQ];
+    typename Pol::R acc[MP][MQ];
 #pragma unroll
     for (int a = 0; a < MP; ++a)
 #pragma unroll
-        for (int c = 0; c < MQ; ++c) acc[a][c] = Acc(0);
+        for (int c = 0; c < MQ; ++c) Pol::zero(acc[a][c]);
     for (int64_t r0 = (int64_t)blockIdx.x * kGramRows; r0 < n;
          r0 += (int64_t)gridDim.x * kGramRows) {
-        stage_cols<T, Acc, TP + 1>(xs, X, r0, n, p0, TP);
-        stage_cols<T, Acc, TQ + 1>(ys, Y, r0, n, q0, TQ);
+        stage_cols<T, T, TP + 1>(xs, X, r0, n, p0, TP);
+        stage_cols<T, T, TQ + 1>(ys, Y, r0, n, q0, TQ);
         __syncthreads();
 #pragma unroll 4
         for (int rr = 0; rr < kGramRows; ++rr) {
-            Acc a[MP], bq[MQ];
+            T a[MP], bq[MQ];
 #pragma unroll
             for (int k = 0; k < MP; ++k) a[k] = xs[rr * (TP + 1) + ti * MP + k];
 #pragma unroll
@@ -193,7 +229,7 @@ k_gram_partial(MB<const T> X, MB<const T> Y, int64_t n, int ntq, Acc* __restrict
 #pragma unroll
             for (int k = 0; k < MP; ++k)
 #pragma unroll
-                for (int l = 0; l < MQ; ++l) acc[k][l] += a[k] * bq[l];
+                for (int l = 0; l < MQ; ++l) Pol::add(acc[k][l], a[k], bq[l]);
         }
         __syncthreads();
     }
@@ -201,7 +237,8 @@ k_gram_partial(MB<const T> X, MB<const T> Y, int64_t n, int ntq, Acc* __restrict
 #pragma unroll
     for (int k = 0; k < MP; ++k)
 #pragma unroll
-        for (int l = 0; l < MQ; ++l) out[(ti * MP + k) * TQ + tj * MQ + l] = acc[k][l];
+        for (int l = 0; l < MQ; ++l)
+            out[(ti * MP + k) * TQ + tj * MQ + l] = Pol::out(acc[k][l]);
 }
 
 // C[(c_row0 + p)*ldc + q] = sum over CTAs of the partials, p < P, q < Q.
@@ -221,19 +258,26 @@ __global__ void k_gram_reduce(const Acc* __restrict__ partials, int g, int ntq, 
 }
 
 // ---------------------------------------------------------------------------------------
-// Block update: OUT = beta*Y + alpha * X C  (CGS step W - Q C, A W - (AQ) C, and W R^{-1})
+// Block update: OUT = beta*Y + alpha * X C  (CGS step W - Q C, and W R^{-1})
 // ---------------------------------------------------------------------------------------
 // X has P <= kPMax columns; C is P x Q with leading dimension ldc starting at row c_row0.
 // upper = 1 when C is upper triangular (only k <= q contributes).  OUT may alias X or Y:
-// each CTA stages its rows of X in shared memory before writing any of them.
+// each CTA stages its kUpdRows rows of X in shared memory before writing any of them.
+// Layout: lane = row of the tile, warp = group of 4 output columns, so the column-dependent
+// trip count of the triangular case is uniform across a warp and the C values a warp reads
+// are broadcasts.
 template <typename T, typename CT>
 __global__ void __launch_bounds__(kThreads)
 k_update(MB<const T> X, const CT* __restrict__ C, int ldc, int c_row0, MB<const T> Y,
          MB<T> OUT, int64_t n, int beta_on, CT alpha, int upper) {
+    static_assert(kUpdRows == 32, "one lane per row");
     extern __shared__ unsigned char smem_raw[];
     T* xs = reinterpret_cast<T*>(smem_raw);
     const int P = X.cols(), Q = OUT.cols();
     const int ldx = P + 1;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    const int ngroups = (Q + 3) >> 2;
+    const CT* Cb = C + (int64_t)c_row0 * ldc;
     for (int64_t r0 = (int64_t)blockIdx.x * kUpdRows; r0 < n;
          r0 += (int64_t)gridDim.x * kUpdRows) {
         for (int e = threadIdx.x; e < kUpdRows * P; e += blockDim.x) {
@@ -243,22 +287,43 @@ k_update(MB<const T> X, const CT* __restrict__ C, int ldc, int c_row0, MB<const 
             xs[rr * ldx + cc] = (row < n) ? X.blk(b)[row * X.w + (cc - b * X.w)] : T(0);
         }
         __syncthreads();
-        for (int e = threadIdx.x; e < kUpdRows * Q; e += blockDim.x) {
-            const int rr = e / Q, q = e - rr * Q;
-            const int64_t row = r0 + rr;
-            if (row < n) {
-                CT acc = CT(0);
-                const int kend = upper ? min(P, q + 1) : P;
-                const T* xr = xs + rr * ldx;
-                const CT* cp = C + (int64_t)c_row0 * ldc + q;
-                for (int k = 0; k < kend; ++k) acc += (CT)xr[k] * cp[(int64_t)k * ldc];
-                const int bo = q / OUT.w, co = q - bo * OUT.w;
-                CT y = CT(0);
-                if (beta_on) {
-                    const int by = q / Y.w;
-                    y = (CT)Y.blk(by)[row * Y.w + (q - by * Y.w)];
+        const int64_t row = r0 + lane;
+        const T* xr = xs + lane * ldx;
+        for (int g = warp; g < ngroups; g += nwarp) {
+            const int q0 = g * 4;
+            const int nq = min(4, Q - q0);
+            const int kend = upper ? min(P, q0 + 4) : P;
+            CT acc0 = CT(0), acc1 = CT(0), acc2 = CT(0), acc3 = CT(0);
+            if (nq == 4) {
+                for (int k = 0; k < kend; ++k) {
+                    const CT xv = (CT)xr[k];
+                    const CT* cr = Cb + (int64_t)k * ldc + q0;
+                    acc0 += xv * cr[0];
+                    acc1 += xv * cr[1];
+                    acc2 += xv * cr[2];
+                    acc3 += xv * cr[3];
                 }
-                OUT.blk(bo)[row * OUT.w + co] = (T)(y + alpha * acc);
+            } else {
+                for (int k = 0; k < kend; ++k) {
+                    const CT xv = (CT)xr[k];
+                    const CT* cr = Cb + (int64_t)k * ldc + q0;
+                    acc0 += xv * cr[0];
+                    if (nq > 1) acc1 += xv * cr[1];
+                    if (nq > 2) acc2 += xv * cr[2];
+                }
+            }
+            if (row < n) {
+                const CT accs[4] = {acc0, acc1, acc2, acc3};
+                for (int c = 0; c < nq; ++c) {
+                    const int q = q0 + c;
+                    const int bo = q / OUT.w, co = q - bo * OUT.w;
+                    CT y = CT(0);
+                    if (beta_on) {
+                        const int by = q / Y.w;
+                        y = (CT)Y.blk(by)[row * Y.w + (q - by * Y.w)];
+                    }
+                    OUT.blk(bo)[row * OUT.w + co] = (T)(y + alpha * accs[c]);
+                }
             }
         }
         __syncthreads();

@@ -87,6 +87,20 @@ def _declare(L):
     L.ekcg_diffusion2d_grad_logkappa.argtypes = [c_void_p, c_int, c_int, c_double, c_double,
                                                  c_void_p, c_void_p, c_void_p, c_void_p]
     L.ekcg_diffusion2d_grad_logkappa.restype = c_int
+    L.ekcg_batched_setup.argtypes = [c_int, c_void_p, c_void_p, c_void_p, c_void_p, c_int,
+                                     c_void_p, POINTER(ekcg_opts), c_void_p, POINTER(c_void_p)]
+    L.ekcg_batched_setup.restype = c_int
+    L.ekcg_batched_solve.argtypes = [c_void_p, c_void_p, c_int, c_double, c_int, c_void_p,
+                                     c_void_p, c_void_p]
+    L.ekcg_batched_solve.restype = c_int
+    L.ekcg_batched_tune.argtypes = [c_void_p, c_void_p, c_int, c_double, c_int]
+    L.ekcg_batched_tune.restype = c_int
+    L.ekcg_batched_info.argtypes = [c_void_p, POINTER(c_int), POINTER(c_int), POINTER(c_double)]
+    L.ekcg_batched_info.restype = c_int
+    L.ekcg_batched_destroy.argtypes = [c_void_p]
+    L.ekcg_batched_destroy.restype = None
+    L.ekcg_batched_last_error.argtypes = []
+    L.ekcg_batched_last_error.restype = c_char_p
 
 
 def lib():
@@ -298,3 +312,67 @@ class Solver:
 
     def profile(self):
         return ekcg_profile(self.ctx)
+
+
+class BatchedSolver:
+    """Many independent systems (a list of workloads.Problem-like objects with .A and .part)
+    solved in one persistent launch (ekcg_batched_*)."""
+
+    def __init__(self, problems, t, precision="fp64", max_s=2, breakdown_tol=1e-14,
+                 inner_tol=1e-4, max_refine=30, stream=None):
+        import torch
+        o = ekcg_default_opts()
+        o.precision = PRECISION[precision]
+        o.max_s, o.breakdown_tol, o.inner_tol, o.max_refine = max_s, breakdown_tol, inner_tol, \
+            max_refine
+        self.sizes = np.array([p.A.n for p in problems], dtype=np.int64)
+        self.offsets = np.concatenate([[0], np.cumsum(self.sizes)])
+        rp = np.concatenate([np.asarray(p.A.rowptr, np.int64) for p in problems])
+        ci = np.concatenate([np.asarray(p.A.colind, np.int32) for p in problems])
+        va = np.concatenate([np.asarray(p.A.val, np.float64) for p in problems])
+        pa = np.concatenate([np.asarray(p.part, np.int32) for p in problems])
+        if stream is None:
+            stream = torch.cuda.current_stream().cuda_stream
+        h = c_void_p()
+        st = lib().ekcg_batched_setup(len(problems), _ptr(self.sizes), _ptr(rp), _ptr(ci),
+                                      _ptr(va), int(t), _ptr(pa), byref(o), c_void_p(stream),
+                                      byref(h))
+        if st != EKCG_OK:
+            raise RuntimeError(f"ekcg_batched_setup: {strerror(st)}: "
+                               f"{lib().ekcg_batched_last_error().decode()}")
+        self.h = h.value
+        self.nsys = len(problems)
+
+    def solve(self, b, s=2, tol=1e-8, maxit=10000, x=None):
+        import torch
+        if x is None:
+            x = torch.empty_like(b)
+        it = np.zeros(self.nsys, dtype=np.int32)
+        stt = np.zeros(self.nsys, dtype=np.int32)
+        st = lib().ekcg_batched_solve(self.h, _ptr(b), int(s), float(tol), int(maxit), _ptr(x),
+                                      _ptr(it), _ptr(stt))
+        if st != EKCG_OK:
+            raise RuntimeError(f"ekcg_batched_solve: {strerror(st)}: "
+                               f"{lib().ekcg_batched_last_error().decode()}")
+        return x, it, stt
+
+    def tune(self, b, s=2, tol=1e-8, maxit=10000):
+        st = lib().ekcg_batched_tune(self.h, _ptr(b), int(s), float(tol), int(maxit))
+        if st != EKCG_OK:
+            raise RuntimeError(lib().ekcg_batched_last_error().decode())
+
+    def info(self):
+        th, cp, ms = c_int(), c_int(), c_double()
+        lib().ekcg_batched_info(self.h, byref(th), byref(cp), byref(ms))
+        return {"threads": th.value, "ctas_per_sm": cp.value, "last_ms": ms.value}
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().ekcg_batched_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

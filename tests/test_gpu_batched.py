@@ -1,0 +1,97 @@
+"""Batched solves (many independent systems, one persistent graph-captured launch) against
+the FP64 oracle, system by system."""
+import os
+
+import numpy as np
+import pytest
+
+import workloads as wl
+from oracle import ekcg_ref as o
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_1804_10629_gb300 import ekcg  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    if not os.path.exists(ekcg.LIB_PATH):
+        from paper_1804_10629_gb300 import build
+        build.build()
+
+
+def small_batch(count=12, seed=11):
+    return wl.batched_systems(count=count, nmin=12, nmax=40, t=8, seed=seed)
+
+
+def concat(probs):
+    return torch.as_tensor(np.concatenate([p.b for p in probs]), dtype=torch.float64,
+                           device="cuda")
+
+
+def split(x, probs):
+    out, o0 = [], 0
+    for p in probs:
+        out.append(x[o0:o0 + p.A.n])
+        o0 += p.A.n
+    return out
+
+
+def test_batched_fp64_matches_oracle_per_system():
+    probs = small_batch()
+    B = ekcg.BatchedSolver(probs, 8, max_s=2)
+    x, it, st = B.solve(concat(probs), s=2, tol=1e-8, maxit=2000)
+    xs = split(x.cpu().numpy(), probs)
+    for k, p in enumerate(probs):
+        ref = o.solve(p.A, p.b, p.part, 8, 2, tol=1e-8, maxit=2000)
+        assert st[k] == ref.status == o.OK, (k, st[k], ref.status)
+        assert abs(int(it[k]) - ref.iters) <= 1, (k, it[k], ref.iters)
+        assert np.linalg.norm(xs[k] - ref.x) <= 1e-8 * np.linalg.norm(ref.x)
+        rr = np.linalg.norm(p.b - p.A.to_scipy() @ xs[k]) / np.linalg.norm(p.b)
+        assert rr <= 1e-8 * 1.01
+    # a second call replays the captured graph and reproduces the result bitwise
+    x2, it2, st2 = B.solve(concat(probs), s=2, tol=1e-8, maxit=2000)
+    assert np.array_equal(x.cpu().numpy(), x2.cpu().numpy()) and np.array_equal(it, it2)
+    B.close()
+
+
+def test_batched_mixed_reaches_tolerance_and_breakdown_is_per_system():
+    probs = small_batch(seed=12)
+    bad = probs[3]
+    bad.b = bad.b.copy()
+    bad.b[bad.part == 5] = 0.0            # T(r_0) has a zero column: breakdown
+    B = ekcg.BatchedSolver(probs, 8, precision="fp32_ir", max_s=2)
+    x, it, st = B.solve(concat(probs), s=2, tol=1e-8, maxit=4000)
+    xs = split(x.cpu().numpy(), probs)
+    for k, p in enumerate(probs):
+        if k == 3:
+            assert st[k] == ekcg.EKCG_EBREAKDOWN
+            continue
+        assert st[k] == 0, (k, st[k])
+        rr = np.linalg.norm(p.b - p.A.to_scipy() @ xs[k]) / np.linalg.norm(p.b)
+        assert rr <= 1e-8 * 1.01, (k, rr)
+    B.close()
+
+
+@pytest.mark.slow
+def test_batched_full_config_true_residuals():
+    """256 systems, grids 32^2..256^2 with coefficient rectangles (jumps up to 1e4), t = 8,
+    s = 2: every system reaches true relres <= 1e-8; the three smallest are compared with
+    the oracle."""
+    probs = wl.batched_systems(count=256, nmin=32, nmax=256, t=8, seed=3)
+    B = ekcg.BatchedSolver(probs, 8, max_s=2)
+    b = concat(probs)
+    B.tune(b, s=2, tol=1e-8, maxit=20000)
+    x, it, st = B.solve(b, s=2, tol=1e-8, maxit=20000)
+    xs = split(x.cpu().numpy(), probs)
+    assert np.all(st == 0)
+    for k, p in enumerate(probs):
+        rr = np.linalg.norm(p.b - p.A.to_scipy() @ xs[k]) / np.linalg.norm(p.b)
+        assert rr <= 1e-8 * 1.01, (k, rr)
+    for k in np.argsort([p.A.n for p in probs])[:3]:
+        p = probs[k]
+        ref = o.solve(p.A, p.b, p.part, 8, 2, tol=1e-8, maxit=20000)
+        assert abs(int(it[k]) - ref.iters) <= 1
+        assert np.linalg.norm(xs[k] - ref.x) <= 1e-8 * np.linalg.norm(ref.x)
+    B.close()
