@@ -47,7 +47,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ekcg", choices=["ekcg", "reference"])
-    ap.add_argument("--workload", default="ani3d", choices=sorted(WORKLOADS) + ["batched"])
+    ap.add_argument("--workload", default="ani3d",
+                    choices=sorted(WORKLOADS) + ["batched", "diff2d"])
     ap.add_argument("--grid", type=int, default=0, help="override the grid side (quick runs)")
     ap.add_argument("--s", type=int, default=0)
     ap.add_argument("--variant", default="")
@@ -111,6 +112,41 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def roofline_and_table(prof, args):
+    """Roofline of the dominant kernel class (by device time) and the per-class table.
+    float64: FP64 ALU bound (alu) for the arithmetic kernels; otherwise the HBM bound."""
+    pk = peaks()
+    hbm = pk.get("hbm_gbs")
+    roof = None
+    if prof:
+        name, d = max(prof.items(), key=lambda kv: kv[1]["ms"])
+        sec = d["ms"] / 1e3
+        if args.precision == "fp64" and name in ("gram", "block_update", "spmm", "chol_inv",
+                                                   "xr_update", "gram_reduce"):
+            ach = d["flops"] / sec / 1e12
+            roof = {"kernel": name, "bound": "alu", "achieved": ach,
+                    "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS,
+                    "peak_source": "derived FP64 FMA rate: 152 SMs x 2 DFMA/clk x 2 x 2.07 GHz",
+                    "traffic": None, "launches": d["launches"],
+                    "avg_launch_ms": d["ms"] / max(d["launches"], 1)}
+        else:
+            peak = hbm or HBM_FALLBACK_GBS
+            ach = d["bytes"] / sec / 1e9
+            roof = {"kernel": name, "bound": "hbm", "achieved": ach, "peak": peak,
+                    "unit": "GB/s", "frac": ach / peak,
+                    "peak_source": "of measured" if hbm else "of fallback",
+                    "traffic": None, "launches": d["launches"],
+                    "avg_launch_ms": d["ms"] / max(d["launches"], 1)}
+    table = {k: {"ms_per_step": v["ms"] / args.steps,
+                 "launches_per_step": v["launches"] / args.steps,
+                 "gflop_per_step": v["flops"] / args.steps / 1e9,
+                 "gb_per_step": v["bytes"] / args.steps / 1e9,
+                 "tflops": (v["flops"] / (v["ms"] / 1e3) / 1e12) if v["ms"] else None,
+                 "gbs": (v["bytes"] / (v["ms"] / 1e3) / 1e9) if v["ms"] else None}
+             for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"])}
+    return roof, table
+
+
 def timed_solves(args, S, b, x, s, stream, dist, clocks):
     """W warm-up solves, then K timed solves bracketed by barrier + synchronize, CUDA events
     on the solve stream; per-kernel-class accounting summed over the timed solves."""
@@ -164,7 +200,8 @@ def run_batched(args, rank, world, dist):
     out = {}
     for prec in ("fp64", "fp32_ir"):
         B = ekcg.BatchedSolver(probs, 8, precision=prec, max_s=s)
-        B.tune(b, s=s, tol=args.tol, maxit=args.maxit)
+        if prec == "fp32_ir":
+            B.tune(b, s=s, tol=args.tol, maxit=args.maxit)
         for _ in range(args.warmup):
             x, it, st = B.solve(b, s=s, tol=args.tol, maxit=args.maxit)
         clocks = Clocks(int(os.environ.get("LOCAL_RANK", "0"))) if prec == "fp64" else None
@@ -208,6 +245,66 @@ def run_batched(args, rank, world, dist):
     return 0
 
 
+def run_diff2d(args, rank, world, dist):
+    """Differentiable configuration: 2D 5-point diffusion on 512^2, log kappa a Gaussian
+    random field (correlation length 16 cells), loss 0.5 ||x - x*||^2 with x* the solution
+    for a second field, b = 1; one step = forward solve + adjoint solve + gradient kernels
+    (dL/db and dL/dlog kappa), t = 16, s = 3, float64."""
+    import torch
+    from paper_1804_10629_gb300 import autograd as ag
+    from paper_1804_10629_gb300 import ekcg
+    N = args.grid or 512
+    s = args.s or 3
+    lk = wl.kappa_gaussian_field2d(N, seed=4, corr=16.0)
+    lk_star = wl.kappa_gaussian_field2d(N, seed=5, corr=16.0)
+    A = wl.stencil_matrix((N, N), kappa=np.exp(lk))
+    part = wl.partition_boxes((N, N), 16)
+    S = ekcg.Solver(A, 16, part, max_s=s)
+    b = torch.ones(N * N, dtype=torch.float64, device="cuda")
+    lks = torch.as_tensor(lk_star.ravel(), device="cuda")
+    with torch.no_grad():
+        xstar = ag.diffusion2d_solve(lks, b, S, N, N, s=s, tol=args.tol)
+
+    def step():
+        lkt = torch.as_tensor(lk.ravel(), device="cuda").clone().requires_grad_(True)
+        bt = b.clone().requires_grad_(True)
+        x = ag.diffusion2d_solve(lkt, bt, S, N, N, s=s, tol=args.tol)
+        loss = 0.5 * ((x - xstar) ** 2).sum()
+        loss.backward()
+        return loss, lkt.grad, bt.grad
+
+    for _ in range(args.warmup):
+        step()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    clocks = Clocks(int(os.environ.get("LOCAL_RANK", "0")))
+    torch.cuda.synchronize()
+    clocks.start()
+    ev0.record()
+    for _ in range(args.steps):
+        loss, g_lk, g_b = step()
+    ev1.record()
+    torch.cuda.synchronize()
+    ck = clocks.stop()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    S.close()
+    if rank == 0:
+        line = {
+            "metric": "time-to-solution @relres 1e-8 (s)", "value": ms / 1e3, "unit": "s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": f"differentiable: 2D diffusion {N}^2, log-kappa Gaussian "
+                                   f"field (corr 16), forward + adjoint solve + gradients, "
+                                   f"t=16, s={s}", "loss": float(loss.item()),
+                       "grad_logkappa_norm": float(g_lk.norm().item()),
+                       "grad_b_norm": float(g_b.norm().item()), "parallelism": "replicas"},
+            "clocks": ck,
+        }
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def dist_setup(args):
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -220,16 +317,17 @@ def oracle_counts():
     return json.load(open(p)) if os.path.exists(p) else {}
 
 
-def cpu_oracle_sample(prob, s, variant, iters, gpu_iters=None):
+def cpu_oracle_sample(prob, s, variant, iters, gpu_iters=None, full_size=True):
     """Time `iters` s-step iterations of the FP64 oracle on the full problem; scale to a
-    whole solve by the oracle's stored iteration count (else the GPU's)."""
+    whole solve by the oracle's stored iteration count (full-size workloads only), else by
+    the GPU's."""
     from oracle import ekcg_ref as o
     t0 = time.perf_counter()
     res = o.solve(prob.A, prob.b, prob.part, prob.t, s, tol=1e-8, maxit=iters, variant=variant)
     dt = time.perf_counter() - t0
     per_it = dt / max(res.iters, 1)
     key = f"{prob.name.split('-')[0].lower()}/t{prob.t}/s{s}/{variant}/sstep/fp64"
-    cnt = oracle_counts().get(key, {}).get("iters")
+    cnt = oracle_counts().get(key, {}).get("iters") if full_size else None
     scale_src = "oracle_counts.json" if cnt else "GPU iteration count"
     total = cnt if cnt else (gpu_iters or res.iters)
     return {"value": per_it * total, "per_iter_s": per_it, "iters_scaled_to": total,
@@ -248,7 +346,8 @@ def run_reference(args, rank, world):
         pass  # the oracle has no warm-up state; warm-up steps would only burn host time
     vals, samples = [], []
     for _ in range(args.steps):
-        r = cpu_oracle_sample(prob, s, variant, args.cpu_sample_iters)
+        r = cpu_oracle_sample(prob, s, variant, args.cpu_sample_iters,
+                              full_size=not args.grid)
         vals.append(r["value"])
         samples.append(r)
     v = statistics.median(vals)
@@ -289,6 +388,8 @@ def main():
 
     if args.workload == "batched":
         return run_batched(args, rank, world, dist)
+    if args.workload == "diff2d":
+        return run_diff2d(args, rank, world, dist)
     cfg = WORKLOADS[args.workload]
     prob = cfg["make"](args.grid)
     s = args.s or cfg["s"]
@@ -335,6 +436,8 @@ def main():
                  "x_rel_diff_vs_fp64": float(np.linalg.norm(xmh - xs) / np.linalg.norm(xs))}
         M.close()
 
+    roof, kernel_table = roofline_and_table(prof, args)
+
     # end to end through the host-buffer C-ABI call (H2D of b and D2H of x inside)
     e2e = None
     if not args.no_e2e:
@@ -349,7 +452,8 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        r = cpu_oracle_sample(prob, s, variant, args.cpu_sample_iters, gpu_iters=its[-1])
+        r = cpu_oracle_sample(prob, s, variant, args.cpu_sample_iters, gpu_iters=its,
+                              full_size=not args.grid)
         cpu = {"value": r["value"], "unit": "s", "cores": r["cores"], "kind": "oracle",
                "sample": f"{r['sample_iters']} s-step iterations of the FP64 oracle on the full "
                          f"workload ({r['sample_s']:.1f} s), scaled to {r['iters_scaled_to']} "
@@ -364,7 +468,7 @@ def main():
             "data": "synthetic",
             "config": {"workload": f"{prob.name} n={prob.A.n} nnz={prob.A.nnz} t={prob.t} "
                                    f"s={s} {variant} {args.basis} {args.precision}",
-                       "desc": cfg["desc"], "tol": args.tol, "iters": its[-1],
+                       "desc": cfg["desc"], "tol": args.tol, "iters": its,
                        "true_relres": relres, "status": st,
                        "l2": "working set larger than L2 (matrix + n x t blocks)",
                        "setup_s": setup_s, "parallelism": "replicas",

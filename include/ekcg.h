@@ -149,6 +149,13 @@ int ekcg_profile(const ekcg_ctx* ctx, int cap, const char** names, double* ms,
  * T: n*t doubles.                                                                         */
 int ekcg_split_T(ekcg_ctx* ctx, const double* r, double* T);
 
+/* C = X^T Y (the block inner products of Section 3.1: CGS coefficients, Gram matrices,
+ * alpha = V^T r): X n x p and Y n x q row-major device doubles, C p x q row-major device
+ * doubles (1 <= p, q <= 256; EKCG_EINVAL if the output tiles exceed the workspace sized
+ * for max_s*t columns).  Two-stage deterministic reduction through the context's
+ * workspace.                                                                             */
+int ekcg_gram(ekcg_ctx* ctx, const double* X, int p, const double* Y, int q, double* C);
+
 /* U = A W for the permuted matrix, W and U n x w row-major doubles (1 <= w <= 256).      */
 int ekcg_spmm(ekcg_ctx* ctx, const double* W, double* U, int w);
 

@@ -230,10 +230,11 @@ struct Shared {
 // s-step SRE-CG on one system in precision T: x (T) from its content, r (T) = residual.
 // Returns the number of iterations; *st receives OK / MAXIT / BREAKDOWN; *rho the final
 // recursive residual norm.
+// stag > 0: stop when no new minimum of rho was reached in the last `stag` iterations.
 template <typename T>
 __device__ int cta_sstep(const Params& P, const Sys& S, T* x, T* r, T* Wb, T* Zb, const T* val,
                          double rho0, double tol_abs, int maxit, Shared& sh, double* scratch,
-                         int* st, double* rho_out) {
+                         int* st, double* rho_out, int stag = 0) {
     const int t = P.t, s = P.s;
     const int64_t n = S.n, slot = n * t;
     const int32_t* rp = P.rowptr + S.rp0;
@@ -242,11 +243,11 @@ __device__ int cta_sstep(const Params& P, const Sys& S, T* x, T* r, T* Wb, T* Zb
     const int ring = s + 2, zring = s + 1;
     auto W = [&](int64_t j) { return Wb + (j % ring) * slot; };
     auto Z = [&](int64_t j) { return Zb + (j % zring) * slot; };
-    double rho = rho0;
-    int k = 1;
+    double rho = rho0, best = rho0;
+    int k = 1, k_best = 0;
     int64_t nb = 0;
     *st = EKCG_OK;
-    while (rho > tol_abs && k < maxit + 1) {
+    while (rho > tol_abs && k < maxit + 1 && !(stag > 0 && k - 1 - k_best >= stag)) {
         const int64_t j0 = nb;
         for (int i = 0; i < s; ++i) {
             const int64_t j = j0 + i;
@@ -321,6 +322,10 @@ __device__ int cta_sstep(const Params& P, const Sys& S, T* x, T* r, T* Wb, T* Zb
             local += (double)ri * (double)ri;
         }
         rho = sqrt(cta_sum(local, sh.red));
+        if (rho < best) {
+            best = rho;
+            k_best = k;
+        }
         ++k;
     }
     if (rho > tol_abs) *st = EKCG_MAXIT;
@@ -387,11 +392,14 @@ __global__ void __launch_bounds__(512) k_batched(Params P) {
                 __syncthreads();
                 int ist = 0;
                 double irho = 0;
-                its += cta_sstep<float>(P, S, d, r32, Wb, Zb, P.val32 + S.nz0, 1.0,
-                                        P.inner_tol, P.maxit - its, sh, scratch, &ist, &irho);
+                // the inner solve reduces r only as far as the outer tolerance still needs
+                const double itol = fmax(P.inner_tol, 0.5 * P.tol * rho0 / rho);
+                its += cta_sstep<float>(P, S, d, r32, Wb, Zb, P.val32 + S.nz0, 1.0, itol,
+                                        P.maxit - its, sh, scratch, &ist, &irho, 30);
                 for (int64_t i = threadIdx.x; i < S.n; i += blockDim.x)
                     P.x[S.row0 + i] += rho * (double)d[i];
                 __syncthreads();
+                const double rho_prev = rho;
                 rho = cta_residual64(P, S, r64);
                 if (!(rho > P.tol * rho0)) {
                     st = EKCG_OK;
@@ -401,6 +409,7 @@ __global__ void __launch_bounds__(512) k_batched(Params P) {
                     st = EKCG_EBREAKDOWN;
                     break;
                 }
+                if (rho > 0.9 * rho_prev) break;   // refinement stagnated: EKCG_MAXIT
             }
         }
         if (threadIdx.x == 0) {

@@ -235,10 +235,70 @@ int gram_shape(ekcg_ctx* c, MB<const T> X, MB<const T> Y, Acc* partials, int* nt
     return EKCG_OK;
 }
 
+// float32 data, exact warp tile, aligned blocks: k_gram_warp_f32.  Returns true if taken.
+template <typename Acc, int LP, int LQ, int MP, int MQ>
+int launch_gram_warp(ekcg_ctx* c, MB<const float> X, MB<const float> Y, Acc* partials, int* g) {
+    constexpr int P = LP * MP, Q = LQ * MQ;
+    const size_t stage = (size_t)4 * 2 * 32 * (P + Q) * sizeof(float);
+    const size_t red = (size_t)4 * P * Q * sizeof(Acc);
+    const size_t smem = stage > red ? stage : red;
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaFuncSetAttribute(k_gram_warp_f32<Acc, LP, LQ, MP, MQ>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        attr_set = true;
+    }
+    *g = (int)std::max<int64_t>(1, std::min<int64_t>((c->n + 127) / 128, (int64_t)c->num_sms * 2));
+    Launch L(c, KC_GRAM, 2.0 * (double)c->n * P * Q, (double)c->n * (P + Q) * sizeof(float));
+    k_gram_warp_f32<Acc, LP, LQ, MP, MQ><<<*g, 128, smem, c->stream>>>(X, Y, c->n, partials);
+    return EKCG_OK;
+}
+
+template <typename T, typename Acc>
+bool gram_fast_path(ekcg_ctx* c, MB<const T> X, MB<const T> Y, Acc* partials, int* g, int* rc) {
+    return false;
+}
+template <typename Acc>
+bool gram_fast_path_f32(ekcg_ctx* c, MB<const float> X, MB<const float> Y, Acc* partials,
+                        int* g, int* rc) {
+    auto al = [](const MB<const float>& m) {
+        return m.w % 4 == 0 && (m.stride % 4) == 0 && ((uintptr_t)m.base % 16) == 0;
+    };
+    if (!al(X) || !al(Y)) return false;
+    const int P = X.cols(), Q = Y.cols();
+    if (P == 64 && Q == 32) { *rc = launch_gram_warp<Acc, 8, 4, 8, 8>(c, X, Y, partials, g); return true; }
+    if (P == 32 && Q == 32) { *rc = launch_gram_warp<Acc, 8, 4, 4, 8>(c, X, Y, partials, g); return true; }
+    if (P == 32 && Q == 16) { *rc = launch_gram_warp<Acc, 8, 4, 4, 4>(c, X, Y, partials, g); return true; }
+    if (P == 16 && Q == 16) { *rc = launch_gram_warp<Acc, 8, 4, 2, 4>(c, X, Y, partials, g); return true; }
+    return false;
+}
+template <>
+bool gram_fast_path<float, float>(ekcg_ctx* c, MB<const float> X, MB<const float> Y,
+                                  float* partials, int* g, int* rc) {
+    return gram_fast_path_f32<float>(c, X, Y, partials, g, rc);
+}
+template <>
+bool gram_fast_path<float, double>(ekcg_ctx* c, MB<const float> X, MB<const float> Y,
+                                   double* partials, int* g, int* rc) {
+    return gram_fast_path_f32<double>(c, X, Y, partials, g, rc);
+}
+
 template <typename T, typename Acc, typename Out>
 int run_gram_chunk(ekcg_ctx* c, MB<const T> X, MB<const T> Y, Out* C, int ldc, int c_row0,
                    Acc* partials) {
     const int P = X.cols(), Q = Y.cols();
+    {
+        int gfast = 0, rc = EKCG_OK;
+        if (gram_fast_path<T, Acc>(c, X, Y, partials, &gfast, &rc)) {
+            if (rc != EKCG_OK) return rc;
+            EK_TRY(check_launch("k_gram_warp_f32"));
+            Launch L(c, KC_REDUCE, (double)gfast * P * Q, (double)gfast * P * Q * sizeof(Acc));
+            int gr = std::max(1, std::min((P * Q + kThreads - 1) / kThreads, c->num_sms * 4));
+            k_gram_reduce<Acc, Out><<<gr, kThreads, 0, c->stream>>>(partials, gfast, 1, P, Q, P,
+                                                                    Q, C, ldc, c_row0);
+            return check_launch("k_gram_reduce");
+        }
+    }
     // tile (TPT*MP) x (TQT*MQ) chosen from P and Q so that no FMA is spent on padding
     int ntq = 1, TP = 64, TQ = 64;
     if (Q > 32) {
@@ -296,10 +356,68 @@ int run_gram(ekcg_ctx* c, MB<const T> X, MB<const T> Y, Out* C, Acc* partials) {
     return EKCG_OK;
 }
 
+// float32, 16-byte-aligned shapes: the register-row kernel (see k_update_f32).
+template <int P>
+int launch_update_f32(ekcg_ctx* c, MB<const float> X, const float* C, int ldc, int c_row0,
+                      MB<const float> Y, MB<float> OUT, int beta_on, float alpha, int upper) {
+    const int g = (int)std::min<int64_t>((c->n + 127) / 128, (int64_t)c->num_sms * 16);
+    k_update_f32<P><<<g, 128, 0, c->stream>>>(X, C, ldc, c_row0, Y, OUT, c->n, beta_on, alpha,
+                                              upper);
+    return EKCG_OK;
+}
+
+template <typename T, typename CT>
+bool update_fast_path(ekcg_ctx* c, MB<const T> X, const CT* C, int ldc, int c_row0,
+                      MB<const T> Y, MB<T> OUT, int beta_on, CT alpha, int upper, int* rc) {
+    return false;
+}
+template <>
+bool update_fast_path<float, float>(ekcg_ctx* c, MB<const float> X, const float* C, int ldc,
+                                    int c_row0, MB<const float> Y, MB<float> OUT, int beta_on,
+                                    float alpha, int upper, int* rc) {
+    const int P = X.cols(), Q = OUT.cols();
+    auto al = [](const MB<const float>& m) {
+        return m.w % 4 == 0 && (m.stride % 4) == 0 &&
+               ((uintptr_t)m.base % 16) == 0;
+    };
+    if (Q % 4 || Q > 64 || !al(X) || !al(as_const(OUT)) || (beta_on && !al(Y))) return false;
+    switch (P) {
+        case 8: *rc = launch_update_f32<8>(c, X, C, ldc, c_row0, Y, OUT, beta_on, alpha, upper); return true;
+        case 16: *rc = launch_update_f32<16>(c, X, C, ldc, c_row0, Y, OUT, beta_on, alpha, upper); return true;
+        case 32: *rc = launch_update_f32<32>(c, X, C, ldc, c_row0, Y, OUT, beta_on, alpha, upper); return true;
+        case 64: *rc = launch_update_f32<64>(c, X, C, ldc, c_row0, Y, OUT, beta_on, alpha, upper); return true;
+        default: return false;
+    }
+}
+
 template <typename T, typename CT>
 int run_update_chunk(ekcg_ctx* c, MB<const T> X, const CT* C, int ldc, int c_row0,
                      MB<const T> Y, MB<T> OUT, int beta_on, CT alpha, int upper) {
     const int P = X.cols();
+    {
+        const int Qo = OUT.cols();
+        const double fl = upper ? (double)c->n * P * (P + 1) : 2.0 * (double)c->n * P * Qo;
+        const double by = (double)c->n * (P + (beta_on ? 2 : 1) * Qo) * sizeof(T);
+        int rc = EKCG_OK;
+        bool done;
+        {
+            Launch L(c, KC_UPDATE, 0.0, 0.0);
+            done = update_fast_path<T, CT>(c, X, C, ldc, c_row0, Y, OUT, beta_on, alpha, upper,
+                                           &rc);
+            if (done) {
+                c->alg_flops[KC_UPDATE] += fl;
+                c->alg_bytes[KC_UPDATE] += by;
+            } else {
+                c->launches--;
+                c->cls_n[KC_UPDATE]--;
+                if (L.idx >= 0) L.idx = -1;
+            }
+        }
+        if (done) {
+            if (rc != EKCG_OK) return rc;
+            return check_launch("k_update_f32");
+        }
+    }
     size_t smem = (size_t)kUpdRows * (P + 1) * sizeof(T);
     int g = (int)std::min<int64_t>((c->n + kUpdRows - 1) / kUpdRows, (int64_t)c->num_sms * 4);
     {
@@ -607,16 +725,20 @@ int run_norm(ekcg_ctx* c, const T* v) {
 //   hist: receives rho_1.. (not rho_0) up to cap; returns status; *iters iterations done.
 //   rho_start = ||r|| on entry; the loop runs while rho > tol_abs and k < maxit + 1.
 //   T(r_0) is taken only in iteration 1, before the first update, so r itself serves.
+//   stag > 0 (inner solves of the refinement loop only): stop when no new minimum of rho
+//   was reached in the last `stag` iterations (float32 stagnation above the tolerance).
 template <typename T>
 int sstep_loop(ekcg_ctx* c, int s, double tol_abs, int maxit, T* x, T* r, double rho_start,
-               double* hist, int cap, int* hlen, int* iters) {
+               double* hist, int cap, int* hlen, int* iters, int stag = 0) {
     Engine<T> E(c, s, x, r);
     int k = 1;
     double rho = rho_start;
+    double best = rho_start;
+    int k_best = 0;
     int status = EKCG_OK;
     *iters = 0;
     int flag = 0;
-    while (rho > tol_abs && k < maxit + 1) {
+    while (rho > tol_abs && k < maxit + 1 && !(stag > 0 && k - 1 - k_best >= stag)) {
         int64_t v0 = 0;
         int rc = (c->opts.basis == EKCG_SSTEP) ? E.iterate_sstep(k, r, &v0)
                                                : E.iterate_ca(k, r, &v0);
@@ -630,6 +752,10 @@ int sstep_loop(ekcg_ctx* c, int s, double tol_abs, int maxit, T* x, T* r, double
         if (*hlen < cap && hist) hist[*hlen] = rho;
         (*hlen)++;
         *iters = k;
+        if (rho < best) {
+            best = rho;
+            k_best = k;
+        }
         k++;
     }
     if (status == EKCG_OK && rho > tol_abs) status = EKCG_MAXIT;
@@ -935,8 +1061,10 @@ int solve_device(ekcg_ctx* c, const double* b, const double* x0, int s, double t
                 }
                 EK_CUDA(cudaMemsetAsync(c->flag, 0, sizeof(int), c->stream));
                 int in_it = 0, in_hl = 0;
-                int rc = sstep_loop<float>(c, s, c->opts.inner_tol, maxit - total, c->x32,
-                                           c->r32, 1.0, nullptr, 0, &in_hl, &in_it);
+                // the inner solve reduces r only as far as the outer tolerance still needs
+                const double itol = std::max(c->opts.inner_tol, 0.5 * tol_abs / rho);
+                int rc = sstep_loop<float>(c, s, itol, maxit - total, c->x32, c->r32, 1.0,
+                                           nullptr, 0, &in_hl, &in_it, 30);
                 total += in_it;
                 if (rc == EKCG_EBREAKDOWN && in_it == 0) {
                     status = EKCG_EBREAKDOWN;
@@ -958,6 +1086,7 @@ int solve_device(ekcg_ctx* c, const double* b, const double* x0, int s, double t
                     Launch L(c, KC_NORM);
                     k_norm_finalize<<<1, 32, 0, c->stream>>>(c->red, c->grid_red, c->rho);
                 }
+                const double rho_prev = rho;
                 EK_TRY(sync_read(c, &rho, &flag));
                 if (hist && hl < cap) hist[hl] = rho;
                 hl++;
@@ -969,6 +1098,7 @@ int solve_device(ekcg_ctx* c, const double* b, const double* x0, int s, double t
                     status = EKCG_EBREAKDOWN;
                     break;
                 }
+                if (rho > 0.9 * rho_prev) break;   // refinement stagnated: EKCG_MAXIT
             }
             it = total;
         }
@@ -1156,6 +1286,18 @@ int ekcg_split_T(ekcg_ctx* c, const double* r, double* T) {
 int ekcg_spmm(ekcg_ctx* c, const double* W, double* U, int w) {
     if (!c || !W || !U || w < 1 || w > 256) return EKCG_EINVAL;
     EK_TRY(run_spmm<double>(c, W, U, w));
+    EK_CUDA(cudaStreamSynchronize(c->stream));
+    return EKCG_OK;
+}
+
+int ekcg_gram(ekcg_ctx* c, const double* X, int p, const double* Y, int q, double* C) {
+    if (!c || !X || !Y || !C || p < 1 || q < 1 || p > kPMax || q > kPMax) {
+        set_error("ekcg_gram", "bad arguments (1 <= p, q <= 256)");
+        return EKCG_EINVAL;
+    }
+    MB<const double> Xm = mb<const double>(X, 0, 0, 1, 1, p);
+    MB<const double> Ym = mb<const double>(Y, 0, 0, 1, 1, q);
+    EK_TRY((run_gram_chunk<double, double, double>(c, Xm, Ym, C, q, 0, c->partials)));
     EK_CUDA(cudaStreamSynchronize(c->stream));
     return EKCG_OK;
 }

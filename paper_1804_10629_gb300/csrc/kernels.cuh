@@ -241,6 +241,125 @@ k_gram_partial(MB<const T> X, MB<const T> Y, int64_t n, int ntq, Acc* __restrict
             out[(ti * MP + k) * TQ + tj * MQ + l] = Pol::out(acc[k][l]);
 }
 
+// float32 Gram for HBM-bound shapes: every warp owns the whole P x Q output (lanes LP x LQ,
+// micro-tile MP x MQ, P = LP*MP and Q = LQ*MQ exactly) and walks its own 32-row groups.
+// Rows are double-buffered into the warp's shared-memory slice with cp.async (16-byte
+// copies, no cross-warp waits), read back as float4, and the warps' tiles are summed in warp
+// order at the end (deterministic).  Block widths must be multiples of 4 floats.
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;"); }
+__device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;"); }
+
+template <typename Acc, int LP, int LQ, int MP, int MQ>
+__global__ void __launch_bounds__(128)
+k_gram_warp_f32(MB<const float> X, MB<const float> Y, int64_t n, Acc* __restrict__ partials) {
+    constexpr int P = LP * MP, Q = LQ * MQ, W = P + Q, kWarps = 4;
+    static_assert(LP * LQ == 32, "one warp");
+    using Pol = GramAcc<float, Acc>;
+    extern __shared__ __align__(16) float gsm[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float* buf = gsm + warp * (2 * 32 * W);        // [2][32 rows][P | Q]
+    const int li = lane / LQ, lj = lane % LQ;
+    typename Pol::R acc[MP][MQ];
+#pragma unroll
+    for (int a = 0; a < MP; ++a)
+#pragma unroll
+        for (int c = 0; c < MQ; ++c) Pol::zero(acc[a][c]);
+    const int64_t groups = (n + 31) / 32;
+    const int64_t gw = (int64_t)gridDim.x * kWarps;
+    int64_t g = (int64_t)blockIdx.x * kWarps + warp;
+    // issue the copies of row group gg into buffer slot sl (rows past n are zero-filled)
+    auto issue = [&](int64_t gg, int sl) {
+        float* dst = buf + sl * 32 * W;
+        const int64_t r0 = gg * 32;
+        const int64_t rem = n - r0;
+        const int rows = rem < 32 ? (int)rem : 32;
+        for (int b = 0; b < X.count; ++b) {
+            const float* src = X.blk(b) + r0 * X.w;
+            const int w4 = X.w / 4;
+            for (int e = lane; e < 32 * w4; e += 32) {
+                const int rr = e / w4, c4 = e - rr * w4;
+                float* d = dst + rr * W + b * X.w + c4 * 4;
+                if (rr < rows)
+                    cp_async16(d, src + rr * X.w + c4 * 4);
+                else
+                    *reinterpret_cast<float4*>(d) = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+        }
+        for (int b = 0; b < Y.count; ++b) {
+            const float* src = Y.blk(b) + r0 * Y.w;
+            const int w4 = Y.w / 4;
+            for (int e = lane; e < 32 * w4; e += 32) {
+                const int rr = e / w4, c4 = e - rr * w4;
+                float* d = dst + rr * W + P + b * Y.w + c4 * 4;
+                if (rr < rows)
+                    cp_async16(d, src + rr * Y.w + c4 * 4);
+                else
+                    *reinterpret_cast<float4*>(d) = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+        }
+    };
+    int slot = 0;
+    if (g < groups) issue(g, 0);
+    cp_async_commit();
+    for (; g < groups; g += gw) {
+        const int64_t nx = g + gw;
+        if (nx < groups) issue(nx, slot ^ 1);
+        cp_async_commit();
+        cp_async_wait1();
+        __syncwarp();
+        const float* cur = buf + slot * 32 * W;
+#pragma unroll 2
+        for (int rr = 0; rr < 32; ++rr) {
+            float a[MP], bq[MQ];
+#pragma unroll
+            for (int k = 0; k < MP; k += (MP % 4 == 0 ? 4 : 1)) {
+                if (MP % 4 == 0) {
+                    const float4 v = *reinterpret_cast<const float4*>(cur + rr * W + li * MP + k);
+                    a[k] = v.x; a[k + 1] = v.y; a[k + 2] = v.z; a[k + 3] = v.w;
+                } else {
+                    a[k] = cur[rr * W + li * MP + k];
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < MQ; k += (MQ % 4 == 0 ? 4 : 1)) {
+                if (MQ % 4 == 0) {
+                    const float4 v = *reinterpret_cast<const float4*>(cur + rr * W + P + lj * MQ + k);
+                    bq[k] = v.x; bq[k + 1] = v.y; bq[k + 2] = v.z; bq[k + 3] = v.w;
+                } else {
+                    bq[k] = cur[rr * W + P + lj * MQ + k];
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < MP; ++k)
+#pragma unroll
+                for (int l = 0; l < MQ; ++l) Pol::add(acc[k][l], a[k], bq[l]);
+        }
+        __syncwarp();
+        slot ^= 1;
+    }
+    cp_async_wait0();
+    __syncthreads();
+    // warp tiles -> shared memory (reusing the staging space), summed in warp order
+    Acc* red = reinterpret_cast<Acc*>(gsm);
+#pragma unroll
+    for (int k = 0; k < MP; ++k)
+#pragma unroll
+        for (int l = 0; l < MQ; ++l)
+            red[warp * P * Q + (li * MP + k) * Q + lj * MQ + l] = Pol::out(acc[k][l]);
+    __syncthreads();
+    Acc* out = partials + (int64_t)blockIdx.x * (kGramTile * kGramTile);
+    for (int e = threadIdx.x; e < P * Q; e += blockDim.x) {
+        Acc s = Acc(0);
+        for (int w = 0; w < kWarps; ++w) s += red[w * P * Q + e];
+        out[e] = s;
+    }
+}
+
 // C[(c_row0 + p)*ldc + q] = sum over CTAs of the partials, p < P, q < Q.
 template <typename Acc, typename Out>
 __global__ void k_gram_reduce(const Acc* __restrict__ partials, int g, int ntq, int TP, int TQ,
@@ -327,6 +446,65 @@ k_update(MB<const T> X, const CT* __restrict__ C, int ldc, int c_row0, MB<const 
             }
         }
         __syncthreads();
+    }
+}
+
+// float32 block update for HBM-bound shapes: one lane per row, the row of X held in
+// registers (16-byte vector loads), C (P x Q <= 64 x 64) in shared memory read as float4
+// broadcasts (4 FMAs per shared load), outputs written as float4.  P and Q multiples of 4,
+// every block width a multiple of 4 (16-byte aligned rows).  OUT may alias X or Y: a lane
+// reads its whole row of X and Y before writing it.
+template <int P>
+__global__ void __launch_bounds__(128)
+k_update_f32(MB<const float> X, const float* __restrict__ C, int ldc, int c_row0,
+             MB<const float> Y, MB<float> OUT, int64_t n, int beta_on, float alpha, int upper) {
+    constexpr int kMaxQ = 64;
+    __shared__ __align__(16) float cs[P * kMaxQ];
+    const int Q = OUT.cols();
+    for (int e = threadIdx.x; e < P * Q; e += blockDim.x) {
+        const int k = e / Q, q = e - k * Q;
+        cs[k * kMaxQ + q] = C[(int64_t)(c_row0 + k) * ldc + q];
+    }
+    __syncthreads();
+    for (int64_t row = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; row < n;
+         row += (int64_t)gridDim.x * blockDim.x) {
+        float x[P];
+#pragma unroll
+        for (int k4 = 0; k4 < P / 4; ++k4) {
+            const int k = k4 * 4, b = k / X.w;
+            const float4 v =
+                *reinterpret_cast<const float4*>(X.blk(b) + row * X.w + (k - b * X.w));
+            x[k] = v.x;
+            x[k + 1] = v.y;
+            x[k + 2] = v.z;
+            x[k + 3] = v.w;
+        }
+        for (int q0 = 0; q0 < Q; q0 += 4) {
+            float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+            const int kend = upper ? min(P, q0 + 4) : P;
+#pragma unroll
+            for (int k = 0; k < P; ++k) {
+                if (k < kend) {
+                    const float4 c = *reinterpret_cast<const float4*>(cs + k * kMaxQ + q0);
+                    acc.x += x[k] * c.x;
+                    acc.y += x[k] * c.y;
+                    acc.z += x[k] * c.z;
+                    acc.w += x[k] * c.w;
+                }
+            }
+            float4 y = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (beta_on) {
+                const int by = q0 / Y.w;
+                y = *reinterpret_cast<const float4*>(Y.blk(by) + row * Y.w + (q0 - by * Y.w));
+            }
+            const int bo = q0 / OUT.w;
+            float4 o;
+            o.x = y.x + alpha * acc.x;
+            o.y = y.y + alpha * acc.y;
+            o.z = y.z + alpha * acc.z;
+            o.w = y.w + alpha * acc.w;
+            *reinterpret_cast<float4*>(OUT.blk(bo) + row * OUT.w + (q0 - bo * OUT.w)) = o;
+        }
     }
 }
 

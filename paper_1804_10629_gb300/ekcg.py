@@ -73,6 +73,8 @@ def _declare(L):
     L.ekcg_profile.restype = c_int
     L.ekcg_split_T.argtypes = [c_void_p, c_void_p, c_void_p]
     L.ekcg_split_T.restype = c_int
+    L.ekcg_gram.argtypes = [c_void_p, c_void_p, c_int, c_void_p, c_int, c_void_p]
+    L.ekcg_gram.restype = c_int
     L.ekcg_spmm.argtypes = [c_void_p, c_void_p, c_void_p, c_int]
     L.ekcg_spmm.restype = c_int
     L.ekcg_permute.argtypes = [c_void_p, c_void_p, c_void_p, c_int]
@@ -225,6 +227,10 @@ def _check(st, where):
 
 def ekcg_split_T(ctx, r, T):
     _check(lib().ekcg_split_T(ctx, _ptr(r), _ptr(T)), "ekcg_split_T")
+
+
+def ekcg_gram(ctx, X, p, Y, q, C):
+    _check(lib().ekcg_gram(ctx, _ptr(X), int(p), _ptr(Y), int(q), _ptr(C)), "ekcg_gram")
 
 
 def ekcg_spmm(ctx, W, U, w):

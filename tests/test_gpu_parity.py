@@ -108,6 +108,22 @@ def test_spmm_matches_scipy(w):
     S.close()
 
 
+@pytest.mark.parametrize("p,q", [(64, 32), (32, 32), (16, 16), (48, 8), (64, 1), (256, 16)])
+def test_gram_entry_matches_numpy(p, q):
+    """C = X^T Y over n = 1665 rows (ragged against the 32-row stages), tolerance
+    n * eps * |X|^T |Y| (the float64 dot-product error bound)."""
+    A = wl.stencil_matrix((45, 37))
+    S = ekcg.Solver(A, 16, wl.partition_boxes((45, 37), 16), max_s=4)
+    rng = np.random.default_rng(p * 1000 + q)
+    X = rng.standard_normal((A.n, p))
+    Y = rng.standard_normal((A.n, q))
+    C = torch.empty(p * q, dtype=torch.float64, device="cuda")
+    ekcg.ekcg_gram(S.ctx, dev(X), p, dev(Y), q, C)
+    bound = A.n * 2.2e-16 * (np.abs(X).T @ np.abs(Y))
+    assert np.all(np.abs(C.cpu().numpy().reshape(p, q) - X.T @ Y) <= bound)
+    S.close()
+
+
 # ----------------------------------------------------------------------------------------
 # Solver parity (ragged sizes: n = 45*37 = 1665 rows is not a multiple of any tile)
 # ----------------------------------------------------------------------------------------
@@ -261,6 +277,25 @@ def test_fp32_ir_reaches_fp64_accuracy(variant):
     S.close()
 
 
+@pytest.mark.parametrize("s", [1, 2])
+def test_fp32_ir_ani3d_t32(s):
+    """t = 32 exercises the float32 register-row update (P = 64 window, P = 32 triangular)
+    and the warp-tile float32 Gram (64 x 32 coefficients, 32 x 32 float-float Gram)."""
+    A = wl.stencil_matrix((24, 24, 24), aniso=(1.0, 1.0, 1e-3))
+    part = wl.partition_boxes((24, 24, 24), 32)
+    b = wl.rhs_uniform(A.n, 1)
+    ref = o.solve(A, b, part, 32, s, tol=1e-8, maxit=1000)
+    S = ekcg.Solver(A, 32, part, precision="fp32_ir", max_s=s)
+    x, it, hist, st = S.solve(dev(b), s=s, tol=1e-8, maxit=5000)
+    x = x.cpu().numpy()
+    assert st == 0
+    assert relres(A, b, x) <= 1e-8 * 1.01
+    lam = np.linalg.eigvalsh(A.to_scipy().toarray())
+    # both relres <= 1e-8: ||x - x_ref|| / ||x_ref|| <= 2e-8 kappa
+    assert np.linalg.norm(x - ref.x) <= 2e-8 * lam[-1] / lam[0] * np.linalg.norm(ref.x)
+    S.close()
+
+
 # ----------------------------------------------------------------------------------------
 # Full-size Ani3D-like 128^3 (the benchmark's launch configuration), sampled checks
 # ----------------------------------------------------------------------------------------
@@ -279,4 +314,11 @@ def test_ani3d_full_size_sampled():
     assert relres(p.A, p.b, x.cpu().numpy()) <= 1e-8 * 1.01
     ref = o.solve(p.A, p.b, p.part, 32, 2, tol=1e-8, maxit=3)
     np.testing.assert_allclose(hist[:4], ref.hist[:4], rtol=1e-6)
+    # whole-solve oracle record (tests/golden/make_oracle_counts.py, oracle only)
+    import json
+    gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden",
+                                       "oracle_counts.json")))
+    g = gold["ani3d/t32/s2/sre/sstep/fp64"]
+    assert abs(it - g["iters"]) <= 1
+    np.testing.assert_allclose(hist[:21], g["hist"][:21], rtol=1e-6)
     S.close()

@@ -119,14 +119,16 @@ def kappa_skyscraper3d(N: int, block: int = 8, high: float = 1e3) -> np.ndarray:
     return np.where(s % 2 == 1, high, 1.0)
 
 
-def kappa_rectangles2d(N: int, rng: np.random.Generator, nrect: int = 4) -> np.ndarray:
-    """Background 1 plus `nrect` axis-aligned rectangles, side U{4..N/2}, value 10^U(0,4)."""
+def kappa_rectangles2d(N: int, rng: np.random.Generator, nrect: int = 4,
+                       contrast: float = 4.0) -> np.ndarray:
+    """Background 1 plus `nrect` axis-aligned rectangles, side U{4..N/2},
+    value 10^U(0, contrast) (contrast 4: jumps up to 1e4)."""
     k = np.ones((N, N))
     for _ in range(nrect):
         wx, wy = rng.integers(4, N // 2 + 1, size=2)
         x0 = rng.integers(0, N - wx + 1)
         y0 = rng.integers(0, N - wy + 1)
-        k[y0:y0 + wy, x0:x0 + wx] = 10.0 ** rng.uniform(0.0, 4.0)
+        k[y0:y0 + wy, x0:x0 + wx] = 10.0 ** rng.uniform(0.0, contrast)
     return k
 
 
@@ -203,14 +205,16 @@ def diffusion2d(N: int, kappa=None, t: int = 16, seed: int = 4) -> Problem:
     return Problem(f"Diff2D-{N}", A, rhs_uniform(A.n, seed), t, partition_boxes((N, N), t), (N, N))
 
 
-def batched_systems(count: int = 256, nmin: int = 32, nmax: int = 256, t: int = 8, seed: int = 3):
+def batched_systems(count: int = 256, nmin: int = 32, nmax: int = 256, t: int = 8, seed: int = 3,
+                    contrast: float = 4.0):
     """`count` independent 2D diffusion systems, grid side N ~ U{nmin..nmax}, four random
-    coefficient rectangles each, 4x2 box partition (t=8), b ~ U(-1,1)."""
+    coefficient rectangles each (values 10^U(0, contrast)), 4x2 box partition (t=8),
+    b ~ U(-1,1)."""
     rng = np.random.Generator(np.random.PCG64(seed))
     out = []
     for k in range(count):
         N = int(rng.integers(nmin, nmax + 1))
-        kap = kappa_rectangles2d(N, rng)
+        kap = kappa_rectangles2d(N, rng, contrast=contrast)
         A = stencil_matrix((N, N), kappa=kap)
         b = rng.uniform(-1.0, 1.0, A.n)
         out.append(Problem(f"batched-{k}-{N}", A, b, t, partition_boxes((N, N), t), (N, N)))
