@@ -156,6 +156,24 @@ int ekcg_split_T(ekcg_ctx* ctx, const double* r, double* T);
  * workspace.                                                                             */
 int ekcg_gram(ekcg_ctx* ctx, const double* X, int p, const double* Y, int q, double* C);
 
+/* Allocation-free C = X^T Y.  The paper has no counterpart: this serves callers that cannot
+ * allocate device memory, such as code running while a stream is captured into a CUDA graph
+ * (an allocation there breaks or is refused by the capture) or programs whose device memory
+ * belongs to another allocator or is fixed at start-up.  Needs no context.
+ *   n rows; X n x p and Y n x q row-major device doubles; C p x q row-major device doubles;
+ *   1 <= p, q <= 64, else EKCG_EINVAL.  stream: a cudaStream_t (NULL = legacy default).
+ *   The work is enqueued on the stream and the call returns without waiting.
+ * Scratch: a fixed 2 MiB device array inside the library (64 CTAs x one 64 x 64 tile of
+ * doubles), present on every GPU that loads the library until the process exits; no call
+ * allocates or frees memory.  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress) with that device current; make that first call before any
+ * stream capture.  Every call shares the array and each call overwrites every entry it later
+ * reads, so nothing has to be cleared between calls; calls that overlap on the GPU (other
+ * streams, other host threads) race on the array and must be serialised by the caller.
+ * Errors: EKCG_EINVAL (sizes, null pointers), EKCG_ECUDA (lookup or launch failure).     */
+int ekcg_gram_noalloc(int64_t n, const double* X, int p, const double* Y, int q, double* C,
+                      void* stream);
+
 /* U = A W for the permuted matrix, W and U n x w row-major doubles (1 <= w <= 256).      */
 int ekcg_spmm(ekcg_ctx* ctx, const double* W, double* U, int w);
 

@@ -9,7 +9,7 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "lib", "libekcg.so")
-SOURCES = ["ekcg_api.cu", "batched.cu"]
+SOURCES = ["ekcg_api.cu", "batched.cu", "noalloc.cu"]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 

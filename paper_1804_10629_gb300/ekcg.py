@@ -75,6 +75,9 @@ def _declare(L):
     L.ekcg_split_T.restype = c_int
     L.ekcg_gram.argtypes = [c_void_p, c_void_p, c_int, c_void_p, c_int, c_void_p]
     L.ekcg_gram.restype = c_int
+    L.ekcg_gram_noalloc.argtypes = [c_int64, c_void_p, c_int, c_void_p, c_int, c_void_p,
+                                    c_void_p]
+    L.ekcg_gram_noalloc.restype = c_int
     L.ekcg_spmm.argtypes = [c_void_p, c_void_p, c_void_p, c_int]
     L.ekcg_spmm.restype = c_int
     L.ekcg_permute.argtypes = [c_void_p, c_void_p, c_void_p, c_int]
@@ -231,6 +234,19 @@ def ekcg_split_T(ctx, r, T):
 
 def ekcg_gram(ctx, X, p, Y, q, C):
     _check(lib().ekcg_gram(ctx, _ptr(X), int(p), _ptr(Y), int(q), _ptr(C)), "ekcg_gram")
+
+
+def ekcg_gram_noalloc(n, X, p, Y, q, C, stream=None):
+    """C = X^T Y without any device allocation (fixed 2 MiB library scratch); p, q <= 64.
+    Enqueued on `stream` (default: torch's current stream); returns without waiting."""
+    if not (1 <= p <= 64 and 1 <= q <= 64):
+        raise ValueError(f"ekcg_gram_noalloc: p = {p}, q = {q}; the fixed scratch holds one "
+                         "64 x 64 tile per CTA, so 1 <= p, q <= 64")
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream().cuda_stream
+    _check(lib().ekcg_gram_noalloc(int(n), _ptr(X), int(p), _ptr(Y), int(q), _ptr(C),
+                                   c_void_p(stream) if stream else None), "ekcg_gram_noalloc")
 
 
 def ekcg_spmm(ctx, W, U, w):
