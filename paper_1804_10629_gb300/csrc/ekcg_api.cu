@@ -200,8 +200,13 @@ int run_spmm(ekcg_ctx* c, const T* W, T* U, int w) {
         const double nnz = (double)c->nnz, nn = (double)c->n;
         Launch L(c, KC_SPMM, 2.0 * nnz * w,
                  nnz * (sizeof(T) + 4.0) + 4.0 * (nn + 1) + 2.0 * nn * w * sizeof(T));
-        k_spmm<T><<<grid_for(c, c->n * w), kThreads, 0, c->stream>>>(U, W, c->rowptr, c->col,
-                                                                    Arena<T>::val(c), c->n, w);
+        const int vn = 16 / (int)sizeof(T);
+        if ((w * (int)sizeof(T)) % 16 == 0 && ((uintptr_t)W % 16) == 0 && ((uintptr_t)U % 16) == 0)
+            k_spmm_vec<T><<<grid_for(c, c->n * (w / vn), 16), 256, 0, c->stream>>>(
+                U, W, c->rowptr, c->col, Arena<T>::val(c), c->n, w);
+        else
+            k_spmm<T><<<grid_for(c, c->n * w), kThreads, 0, c->stream>>>(
+                U, W, c->rowptr, c->col, Arena<T>::val(c), c->n, w);
     }
     c->spmm_calls++;
     return check_launch("k_spmm");

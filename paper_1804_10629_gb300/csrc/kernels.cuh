@@ -137,6 +137,64 @@ __global__ void k_spmm(T* __restrict__ U, const T* __restrict__ W,
     }
 }
 
+// Vectorised variant: each thread owns 16 bytes of an output row (4 floats or 2 doubles);
+// threads of a row share the row's (col, val) loads through L1.  Needs w * sizeof(T) a
+// multiple of 16 and 16-byte aligned W and U.
+template <typename T>
+struct Vec16;
+template <>
+struct Vec16<float> {
+    using V = float4;
+    static constexpr int N = 4;
+    __device__ __forceinline__ static void fma(V& a, float s, const V& b) {
+        a.x += s * b.x; a.y += s * b.y; a.z += s * b.z; a.w += s * b.w;
+    }
+    __device__ __forceinline__ static V zero() { return make_float4(0.f, 0.f, 0.f, 0.f); }
+};
+template <>
+struct Vec16<double> {
+    using V = double2;
+    static constexpr int N = 2;
+    __device__ __forceinline__ static void fma(V& a, double s, const V& b) {
+        a.x += s * b.x; a.y += s * b.y;
+    }
+    __device__ __forceinline__ static V zero() { return make_double2(0.0, 0.0); }
+};
+
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_spmm_vec(T* __restrict__ U, const T* __restrict__ W, const int32_t* __restrict__ rowptr,
+           const int32_t* __restrict__ col, const T* __restrict__ val, int64_t n, int w) {
+    using VT = Vec16<T>;
+    using V = typename VT::V;
+    const int nv = w / VT::N;                 // vectors per row
+    const int64_t total = n * nv;
+    const V* Wv = reinterpret_cast<const V*>(W);
+    V* Uv = reinterpret_cast<V*>(U);
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = e / nv;
+        const int c = (int)(e - i * nv);
+        const int j0 = __ldg(rowptr + i), j1 = __ldg(rowptr + i + 1);
+        V acc = VT::zero();
+        int j = j0;
+        for (; j + 4 <= j1; j += 4) {
+            const int c0 = __ldg(col + j), c1 = __ldg(col + j + 1), c2 = __ldg(col + j + 2),
+                      c3 = __ldg(col + j + 3);
+            const T v0 = __ldg(val + j), v1 = __ldg(val + j + 1), v2 = __ldg(val + j + 2),
+                    v3 = __ldg(val + j + 3);
+            const V w0 = Wv[(int64_t)c0 * nv + c], w1 = Wv[(int64_t)c1 * nv + c],
+                    w2 = Wv[(int64_t)c2 * nv + c], w3 = Wv[(int64_t)c3 * nv + c];
+            VT::fma(acc, v0, w0);
+            VT::fma(acc, v1, w1);
+            VT::fma(acc, v2, w2);
+            VT::fma(acc, v3, w3);
+        }
+        for (; j < j1; ++j) VT::fma(acc, __ldg(val + j), Wv[(int64_t)__ldg(col + j) * nv + c]);
+        Uv[e] = acc;
+    }
+}
+
 // ---------------------------------------------------------------------------------------
 // Tall-skinny products C = X^T Y (Gram matrices, CGS coefficients, alpha = V^T r)
 // ---------------------------------------------------------------------------------------

@@ -322,3 +322,23 @@ def test_ani3d_full_size_sampled():
     assert abs(it - g["iters"]) <= 1
     np.testing.assert_allclose(hist[:21], g["hist"][:21], rtol=1e-6)
     S.close()
+
+
+@pytest.mark.slow
+def test_sky3d_full_size_against_oracle_record():
+    """Sky3D-like 96^3 (coefficient 1 / 1e3 on 8^3 blocks), t = 16, s = 4, float64: the
+    iteration count and the first 21 residual norms against the oracle's whole-solve
+    record (tests/golden/oracle_counts.json, written by the oracle only), and the true
+    relative residual."""
+    import json
+    gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden",
+                                       "oracle_counts.json")))
+    g = gold["sky3d/t16/s4/sre/sstep/fp64"]
+    p = wl.sky3d(96, 16, seed=2)
+    S = ekcg.Solver(p.A, 16, p.part, max_s=4)
+    x, it, hist, st = S.solve(dev(p.b), s=4, tol=1e-8, maxit=5000)
+    assert st == 0
+    assert abs(it - g["iters"]) <= 1, (it, g["iters"])
+    np.testing.assert_allclose(hist[:21], g["hist"][:21], rtol=1e-6)
+    assert relres(p.A, p.b, x.cpu().numpy()) <= 1e-8 * 1.01
+    S.close()
