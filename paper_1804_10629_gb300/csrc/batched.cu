@@ -94,6 +94,33 @@ __device__ void cta_spmm(T* __restrict__ U, const T* __restrict__ W, const int32
     }
 }
 
+// Float-float accumulation (about 48 significant bits): the float product is made exact
+// with an FMA and added with TwoSum.  Used when float32 data must give a float64-grade sum.
+struct DFAcc {
+    float hi = 0.f, lo = 0.f;
+    __device__ __forceinline__ void add(float a, float b) {
+        const float p = a * b;
+        const float e = fmaf(a, b, -p);
+        const float s = hi + p;
+        const float v = s - hi;
+        lo += ((hi - (s - v)) + (p - v)) + e;
+        hi = s;
+    }
+    __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+template <typename T, typename Acc>
+struct CtaAcc {
+    Acc a = Acc(0);
+    __device__ __forceinline__ void add(T x, T y) { a += (Acc)x * (Acc)y; }
+    __device__ __forceinline__ double value() const { return (double)a; }
+};
+template <>
+struct CtaAcc<float, double> {
+    DFAcc a;
+    __device__ __forceinline__ void add(float x, float y) { a.add(x, y); }
+    __device__ __forceinline__ double value() const { return a.value(); }
+};
+
 // C[p*Q + q] = sum_rows X_p[row] Y_q[row] (accumulated in Acc, stored as double); X is nx
 // blocks (n x t), Y is ny blocks of ty columns.  With fewer outputs than threads, each output
 // is split over row stripes reduced in stripe order (deterministic).
@@ -108,15 +135,15 @@ __device__ void cta_gram(double* C, const T* const* X, int nx, const T* const* Y
             const T* xb = X[p / t];
             const T* yb = Y[q / ty];
             const int xc = p % t, yc = q % ty;
-            Acc acc = Acc(0);
-            for (int64_t row = 0; row < n; ++row) acc += (Acc)xb[row * t + xc] * (Acc)yb[row * ty + yc];
-            C[o] = (double)acc;
+            CtaAcc<T, Acc> acc;
+            for (int64_t row = 0; row < n; ++row) acc.add(xb[row * t + xc], yb[row * ty + yc]);
+            C[o] = acc.value();
         }
         __syncthreads();
         return;
     }
     const int stripes = (int)blockDim.x / PQ;
-    Acc acc = Acc(0);
+    CtaAcc<T, Acc> acc;
     const bool active = tid < PQ * stripes;
     if (active) {
         const int o = tid % PQ, st = tid / PQ;
@@ -124,11 +151,10 @@ __device__ void cta_gram(double* C, const T* const* X, int nx, const T* const* Y
         const T* xb = X[p / t];
         const T* yb = Y[q / ty];
         const int xc = p % t, yc = q % ty;
-        for (int64_t row = st; row < n; row += stripes)
-            acc += (Acc)xb[row * t + xc] * (Acc)yb[row * ty + yc];
+        for (int64_t row = st; row < n; row += stripes) acc.add(xb[row * t + xc], yb[row * ty + yc]);
     }
     __syncthreads();
-    if (active) scratch[tid] = (double)acc;
+    if (active) scratch[tid] = acc.value();
     __syncthreads();
     for (int o = tid; o < PQ; o += blockDim.x) {
         double s = 0.0;
@@ -247,7 +273,8 @@ __device__ int cta_sstep(const Params& P, const Sys& S, T* x, T* r, T* Wb, T* Zb
     int k = 1, k_best = 0;
     int64_t nb = 0;
     *st = EKCG_OK;
-    while (rho > tol_abs && k < maxit + 1 && !(stag > 0 && k - 1 - k_best >= stag)) {
+    while (rho > tol_abs && k < maxit + 1 &&
+           !(stag > 0 && k - 1 - k_best >= max(stag, k_best / 2))) {
         const int64_t j0 = nb;
         for (int i = 0; i < s; ++i) {
             const int64_t j = j0 + i;
@@ -395,7 +422,7 @@ __global__ void __launch_bounds__(512) k_batched(Params P) {
                 // the inner solve reduces r only as far as the outer tolerance still needs
                 const double itol = fmax(P.inner_tol, 0.5 * P.tol * rho0 / rho);
                 its += cta_sstep<float>(P, S, d, r32, Wb, Zb, P.val32 + S.nz0, 1.0, itol,
-                                        P.maxit - its, sh, scratch, &ist, &irho, 30);
+                                        P.maxit - its, sh, scratch, &ist, &irho, 50);
                 for (int64_t i = threadIdx.x; i < S.n; i += blockDim.x)
                     P.x[S.row0 + i] += rho * (double)d[i];
                 __syncthreads();

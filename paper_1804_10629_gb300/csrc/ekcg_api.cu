@@ -244,7 +244,7 @@ int gram_shape(ekcg_ctx* c, MB<const T> X, MB<const T> Y, Acc* partials, int* nt
 template <typename Acc, int LP, int LQ, int MP, int MQ>
 int launch_gram_warp(ekcg_ctx* c, MB<const float> X, MB<const float> Y, Acc* partials, int* g) {
     constexpr int P = LP * MP, Q = LQ * MQ;
-    const size_t stage = (size_t)4 * 2 * 32 * (P + Q) * sizeof(float);
+    const size_t stage = (size_t)4 * 2 * 16 * ((P + Q + 3) / 4 * 4) * sizeof(float);
     const size_t red = (size_t)4 * P * Q * sizeof(Acc);
     const size_t smem = stage > red ? stage : red;
     static bool attr_set = false;
@@ -269,8 +269,14 @@ bool gram_fast_path_f32(ekcg_ctx* c, MB<const float> X, MB<const float> Y, Acc* 
     auto al = [](const MB<const float>& m) {
         return m.w % 4 == 0 && (m.stride % 4) == 0 && ((uintptr_t)m.base % 16) == 0;
     };
-    if (!al(X) || !al(Y)) return false;
     const int P = X.cols(), Q = Y.cols();
+    // alpha = V^T r: one right-hand column (4-byte copies for it)
+    if (Q == 1 && Y.count == 1 && al(X) && ((uintptr_t)Y.base % 4) == 0) {
+        if (P == 64) { *rc = launch_gram_warp<Acc, 32, 1, 2, 1>(c, X, Y, partials, g); return true; }
+        if (P == 32) { *rc = launch_gram_warp<Acc, 32, 1, 1, 1>(c, X, Y, partials, g); return true; }
+        return false;
+    }
+    if (!al(X) || !al(Y)) return false;
     if (P == 64 && Q == 32) { *rc = launch_gram_warp<Acc, 8, 4, 8, 8>(c, X, Y, partials, g); return true; }
     if (P == 32 && Q == 32) { *rc = launch_gram_warp<Acc, 8, 4, 4, 8>(c, X, Y, partials, g); return true; }
     if (P == 32 && Q == 16) { *rc = launch_gram_warp<Acc, 8, 4, 4, 4>(c, X, Y, partials, g); return true; }
@@ -385,7 +391,7 @@ bool update_fast_path<float, float>(ekcg_ctx* c, MB<const float> X, const float*
         return m.w % 4 == 0 && (m.stride % 4) == 0 &&
                ((uintptr_t)m.base % 16) == 0;
     };
-    if (Q % 4 || Q > 64 || !al(X) || !al(as_const(OUT)) || (beta_on && !al(Y))) return false;
+    if (Q % 4 || Q > 32 || !al(X) || !al(as_const(OUT)) || (beta_on && !al(Y))) return false;
     switch (P) {
         case 8: *rc = launch_update_f32<8>(c, X, C, ldc, c_row0, Y, OUT, beta_on, alpha, upper); return true;
         case 16: *rc = launch_update_f32<16>(c, X, C, ldc, c_row0, Y, OUT, beta_on, alpha, upper); return true;
@@ -743,7 +749,8 @@ int sstep_loop(ekcg_ctx* c, int s, double tol_abs, int maxit, T* x, T* r, double
     int status = EKCG_OK;
     *iters = 0;
     int flag = 0;
-    while (rho > tol_abs && k < maxit + 1 && !(stag > 0 && k - 1 - k_best >= stag)) {
+    while (rho > tol_abs && k < maxit + 1 &&
+           !(stag > 0 && k - 1 - k_best >= std::max(stag, k_best / 2))) {
         int64_t v0 = 0;
         int rc = (c->opts.basis == EKCG_SSTEP) ? E.iterate_sstep(k, r, &v0)
                                                : E.iterate_ca(k, r, &v0);
@@ -1069,7 +1076,7 @@ int solve_device(ekcg_ctx* c, const double* b, const double* x0, int s, double t
                 // the inner solve reduces r only as far as the outer tolerance still needs
                 const double itol = std::max(c->opts.inner_tol, 0.5 * tol_abs / rho);
                 int rc = sstep_loop<float>(c, s, itol, maxit - total, c->x32, c->r32, 1.0,
-                                           nullptr, 0, &in_hl, &in_it, 30);
+                                           nullptr, 0, &in_hl, &in_it, 50);
                 total += in_it;
                 if (rc == EKCG_EBREAKDOWN && in_it == 0) {
                     status = EKCG_EBREAKDOWN;

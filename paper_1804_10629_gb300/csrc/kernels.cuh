@@ -315,51 +315,59 @@ __device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_g
 template <typename Acc, int LP, int LQ, int MP, int MQ>
 __global__ void __launch_bounds__(128)
 k_gram_warp_f32(MB<const float> X, MB<const float> Y, int64_t n, Acc* __restrict__ partials) {
-    constexpr int P = LP * MP, Q = LQ * MQ, W = P + Q, kWarps = 4;
+    // W: shared row stride, padded to 4 floats so every 16-byte copy stays aligned
+    constexpr int P = LP * MP, Q = LQ * MQ, W = (P + Q + 3) / 4 * 4, kWarps = 4, RG = 16;
+    static_assert(P % 4 == 0, "X part of a staged row must be 16-byte aligned");
     static_assert(LP * LQ == 32, "one warp");
     using Pol = GramAcc<float, Acc>;
     extern __shared__ __align__(16) float gsm[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    float* buf = gsm + warp * (2 * 32 * W);        // [2][32 rows][P | Q]
+    float* buf = gsm + warp * (2 * RG * W);        // [2][RG rows][P | Q]
     const int li = lane / LQ, lj = lane % LQ;
     typename Pol::R acc[MP][MQ];
 #pragma unroll
     for (int a = 0; a < MP; ++a)
 #pragma unroll
         for (int c = 0; c < MQ; ++c) Pol::zero(acc[a][c]);
-    const int64_t groups = (n + 31) / 32;
+    const int64_t groups = (n + RG - 1) / RG;
     const int64_t gw = (int64_t)gridDim.x * kWarps;
     int64_t g = (int64_t)blockIdx.x * kWarps + warp;
-    // issue the copies of row group gg into buffer slot sl (rows past n are zero-filled)
+    // copies of row group gg into slot sl; rows past n are zero-filled
+    auto stage_op = [&](const MB<const float>& M, int col0, int64_t r0, int rows, float* dst) {
+        for (int b = 0; b < M.count; ++b) {
+            const float* src = M.blk(b) + r0 * M.w;
+            if (M.w % 4 == 0) {
+                const int w4 = M.w / 4;
+                for (int e = lane; e < RG * w4; e += 32) {
+                    const int rr = e / w4, c4 = e - rr * w4;
+                    float* d = dst + rr * W + col0 + b * M.w + c4 * 4;
+                    if (rr < rows)
+                        cp_async16(d, src + rr * M.w + c4 * 4);
+                    else
+                        *reinterpret_cast<float4*>(d) = make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+            } else {
+                for (int e = lane; e < RG * M.w; e += 32) {
+                    const int rr = e / M.w, cc = e - rr * M.w;
+                    float* d = dst + rr * W + col0 + b * M.w + cc;
+                    if (rr < rows) {
+                        const unsigned sa = (unsigned)__cvta_generic_to_shared(d);
+                        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(sa),
+                                     "l"(src + rr * M.w + cc) : "memory");
+                    } else {
+                        *d = 0.f;
+                    }
+                }
+            }
+        }
+    };
     auto issue = [&](int64_t gg, int sl) {
-        float* dst = buf + sl * 32 * W;
-        const int64_t r0 = gg * 32;
+        float* dst = buf + sl * RG * W;
+        const int64_t r0 = gg * RG;
         const int64_t rem = n - r0;
-        const int rows = rem < 32 ? (int)rem : 32;
-        for (int b = 0; b < X.count; ++b) {
-            const float* src = X.blk(b) + r0 * X.w;
-            const int w4 = X.w / 4;
-            for (int e = lane; e < 32 * w4; e += 32) {
-                const int rr = e / w4, c4 = e - rr * w4;
-                float* d = dst + rr * W + b * X.w + c4 * 4;
-                if (rr < rows)
-                    cp_async16(d, src + rr * X.w + c4 * 4);
-                else
-                    *reinterpret_cast<float4*>(d) = make_float4(0.f, 0.f, 0.f, 0.f);
-            }
-        }
-        for (int b = 0; b < Y.count; ++b) {
-            const float* src = Y.blk(b) + r0 * Y.w;
-            const int w4 = Y.w / 4;
-            for (int e = lane; e < 32 * w4; e += 32) {
-                const int rr = e / w4, c4 = e - rr * w4;
-                float* d = dst + rr * W + P + b * Y.w + c4 * 4;
-                if (rr < rows)
-                    cp_async16(d, src + rr * Y.w + c4 * 4);
-                else
-                    *reinterpret_cast<float4*>(d) = make_float4(0.f, 0.f, 0.f, 0.f);
-            }
-        }
+        const int rows = rem < RG ? (int)rem : RG;
+        stage_op(X, 0, r0, rows, dst);
+        stage_op(Y, P, r0, rows, dst);
     };
     int slot = 0;
     if (g < groups) issue(g, 0);
@@ -370,9 +378,9 @@ k_gram_warp_f32(MB<const float> X, MB<const float> Y, int64_t n, Acc* __restrict
         cp_async_commit();
         cp_async_wait1();
         __syncwarp();
-        const float* cur = buf + slot * 32 * W;
+        const float* cur = buf + slot * RG * W;
 #pragma unroll 2
-        for (int rr = 0; rr < 32; ++rr) {
+        for (int rr = 0; rr < RG; ++rr) {
             float a[MP], bq[MQ];
 #pragma unroll
             for (int k = 0; k < MP; k += (MP % 4 == 0 ? 4 : 1)) {
@@ -516,7 +524,7 @@ template <int P>
 __global__ void __launch_bounds__(128)
 k_update_f32(MB<const float> X, const float* __restrict__ C, int ldc, int c_row0,
              MB<const float> Y, MB<float> OUT, int64_t n, int beta_on, float alpha, int upper) {
-    constexpr int kMaxQ = 64;
+    constexpr int kMaxQ = 32, KC = 16;
     __shared__ __align__(16) float cs[P * kMaxQ];
     const int Q = OUT.cols();
     for (int e = threadIdx.x; e < P * Q; e += blockDim.x) {
@@ -524,44 +532,58 @@ k_update_f32(MB<const float> X, const float* __restrict__ C, int ldc, int c_row0
         cs[k * kMaxQ + q] = C[(int64_t)(c_row0 + k) * ldc + q];
     }
     __syncthreads();
+    const int nq4 = Q / 4;
     for (int64_t row = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; row < n;
          row += (int64_t)gridDim.x * blockDim.x) {
-        float x[P];
+        float4 acc[kMaxQ / 4];
 #pragma unroll
-        for (int k4 = 0; k4 < P / 4; ++k4) {
-            const int k = k4 * 4, b = k / X.w;
-            const float4 v =
-                *reinterpret_cast<const float4*>(X.blk(b) + row * X.w + (k - b * X.w));
-            x[k] = v.x;
-            x[k + 1] = v.y;
-            x[k + 2] = v.z;
-            x[k + 3] = v.w;
-        }
-        for (int q0 = 0; q0 < Q; q0 += 4) {
-            float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-            const int kend = upper ? min(P, q0 + 4) : P;
+        for (int q4 = 0; q4 < kMaxQ / 4; ++q4) acc[q4] = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-            for (int k = 0; k < P; ++k) {
-                if (k < kend) {
-                    const float4 c = *reinterpret_cast<const float4*>(cs + k * kMaxQ + q0);
-                    acc.x += x[k] * c.x;
-                    acc.y += x[k] * c.y;
-                    acc.z += x[k] * c.z;
-                    acc.w += x[k] * c.w;
+        for (int k0 = 0; k0 < P; k0 += (P < KC ? P : KC)) {
+            constexpr int KK = P < KC ? P : KC;
+            float x[KK];
+#pragma unroll
+            for (int k4 = 0; k4 < KK / 4; ++k4) {
+                const int k = k0 + k4 * 4, b = k / X.w;
+                const float4 v =
+                    *reinterpret_cast<const float4*>(X.blk(b) + row * X.w + (k - b * X.w));
+                x[k4 * 4] = v.x;
+                x[k4 * 4 + 1] = v.y;
+                x[k4 * 4 + 2] = v.z;
+                x[k4 * 4 + 3] = v.w;
+            }
+#pragma unroll
+            for (int q4 = 0; q4 < kMaxQ / 4; ++q4) {
+                if (q4 < nq4 && (!upper || k0 <= q4 * 4 + 3)) {
+#pragma unroll
+                    for (int kk = 0; kk < KK; ++kk) {
+                        const float4 c =
+                            *reinterpret_cast<const float4*>(cs + (k0 + kk) * kMaxQ + q4 * 4);
+                        acc[q4].x += x[kk] * c.x;
+                        acc[q4].y += x[kk] * c.y;
+                        acc[q4].z += x[kk] * c.z;
+                        acc[q4].w += x[kk] * c.w;
+                    }
                 }
             }
-            float4 y = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (beta_on) {
-                const int by = q0 / Y.w;
-                y = *reinterpret_cast<const float4*>(Y.blk(by) + row * Y.w + (q0 - by * Y.w));
+        }
+#pragma unroll
+        for (int q4 = 0; q4 < kMaxQ / 4; ++q4) {
+            if (q4 < nq4) {
+                const int q0 = q4 * 4;
+                float4 y = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (beta_on) {
+                    const int by = q0 / Y.w;
+                    y = *reinterpret_cast<const float4*>(Y.blk(by) + row * Y.w + (q0 - by * Y.w));
+                }
+                const int bo = q0 / OUT.w;
+                float4 o;
+                o.x = y.x + alpha * acc[q4].x;
+                o.y = y.y + alpha * acc[q4].y;
+                o.z = y.z + alpha * acc[q4].z;
+                o.w = y.w + alpha * acc[q4].w;
+                *reinterpret_cast<float4*>(OUT.blk(bo) + row * OUT.w + (q0 - bo * OUT.w)) = o;
             }
-            const int bo = q0 / OUT.w;
-            float4 o;
-            o.x = y.x + alpha * acc.x;
-            o.y = y.y + alpha * acc.y;
-            o.z = y.z + alpha * acc.z;
-            o.w = y.w + alpha * acc.w;
-            *reinterpret_cast<float4*>(OUT.blk(bo) + row * OUT.w + (q0 - bo * OUT.w)) = o;
         }
     }
 }
