@@ -253,7 +253,10 @@ int launch_gram_warp(ekcg_ctx* c, MB<const float> X, MB<const float> Y, Acc* par
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         attr_set = true;
     }
-    *g = (int)std::max<int64_t>(1, std::min<int64_t>((c->n + 127) / 128, (int64_t)c->num_sms * 2));
+    // up to 4 CTAs per SM; every CTA writes one partial tile, which the workspace holds
+    const int64_t gcap = std::min<int64_t>((int64_t)c->num_sms * 4,
+                                           c->cap_partials / (kGramTile * kGramTile));
+    *g = (int)std::max<int64_t>(1, std::min<int64_t>((c->n + 63) / 64, gcap));
     Launch L(c, KC_GRAM, 2.0 * (double)c->n * P * Q, (double)c->n * (P + Q) * sizeof(float));
     k_gram_warp_f32<Acc, LP, LQ, MP, MQ><<<*g, 128, smem, c->stream>>>(X, Y, c->n, partials);
     return EKCG_OK;
@@ -371,8 +374,9 @@ int run_gram(ekcg_ctx* c, MB<const T> X, MB<const T> Y, Out* C, Acc* partials) {
 template <int P>
 int launch_update_f32(ekcg_ctx* c, MB<const float> X, const float* C, int ldc, int c_row0,
                       MB<const float> Y, MB<float> OUT, int beta_on, float alpha, int upper) {
-    const int g = (int)std::min<int64_t>((c->n + 127) / 128, (int64_t)c->num_sms * 16);
-    k_update_f32<P><<<g, 128, 0, c->stream>>>(X, C, ldc, c_row0, Y, OUT, c->n, beta_on, alpha,
+    const int64_t work = c->n * (OUT.cols() / 4);
+    const int g = (int)std::min<int64_t>((work + 255) / 256, (int64_t)c->num_sms * 8);
+    k_update_f32<P><<<g, 256, 0, c->stream>>>(X, C, ldc, c_row0, Y, OUT, c->n, beta_on, alpha,
                                               upper);
     return EKCG_OK;
 }
@@ -392,6 +396,24 @@ bool update_fast_path<float, float>(ekcg_ctx* c, MB<const float> X, const float*
                ((uintptr_t)m.base % 16) == 0;
     };
     if (Q % 4 || Q > 32 || !al(X) || !al(as_const(OUT)) || (beta_on && !al(Y))) return false;
+    // in place on X (W <- W R^{-1}): the warp-synchronous triangular kernel
+    bool inplace = false;
+    for (int a = 0; a < X.count; ++a)
+        for (int b = 0; b < OUT.count; ++b)
+            if (X.blk(a) == (const float*)OUT.blk(b)) inplace = true;
+    if (inplace) {
+        if (!upper || beta_on || P != Q || alpha != 1.f || X.count != OUT.count) return false;
+        const int64_t work = c->n * (Q / 4);
+        const int g = (int)std::min<int64_t>((work + 255) / 256, (int64_t)c->num_sms * 8);
+        switch (P) {
+            case 8: k_rmul_f32<8><<<g, 256, 0, c->stream>>>(OUT, C + (int64_t)c_row0 * ldc, ldc, c->n); break;
+            case 16: k_rmul_f32<16><<<g, 256, 0, c->stream>>>(OUT, C + (int64_t)c_row0 * ldc, ldc, c->n); break;
+            case 32: k_rmul_f32<32><<<g, 256, 0, c->stream>>>(OUT, C + (int64_t)c_row0 * ldc, ldc, c->n); break;
+            default: return false;
+        }
+        *rc = EKCG_OK;
+        return true;
+    }
     switch (P) {
         case 8: *rc = launch_update_f32<8>(c, X, C, ldc, c_row0, Y, OUT, beta_on, alpha, upper); return true;
         case 16: *rc = launch_update_f32<16>(c, X, C, ldc, c_row0, Y, OUT, beta_on, alpha, upper); return true;

@@ -515,16 +515,19 @@ k_update(MB<const T> X, const CT* __restrict__ C, int ldc, int c_row0, MB<const 
     }
 }
 
-// float32 block update for HBM-bound shapes: one lane per row, the row of X held in
-// registers (16-byte vector loads), C (P x Q <= 64 x 64) in shared memory read as float4
-// broadcasts (4 FMAs per shared load), outputs written as float4.  P and Q multiples of 4,
-// every block width a multiple of 4 (16-byte aligned rows).  OUT may alias X or Y: a lane
-// reads its whole row of X and Y before writing it.
+// float32 block update for HBM-bound shapes: each thread owns one row and 4 consecutive
+// output columns.  The Q/4 threads of a row read the row of X as the same float4 values
+// (broadcast through L1), C (P x Q <= 64 x 32) sits in shared memory and is read as float4,
+// and Y / OUT are read and written as float4 runs along the row (coalesced).  The
+// triangular case runs the full loop over the zero part of C: the threads of a warp would
+// wait for the longest one anyway.  P, Q and every block width are multiples of 4 (16-byte
+// aligned rows).  OUT may alias Y (each thread reads its own float4 of Y before writing it);
+// OUT aliasing X is not allowed here (rows of X are read by several threads).
 template <int P>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(256)
 k_update_f32(MB<const float> X, const float* __restrict__ C, int ldc, int c_row0,
              MB<const float> Y, MB<float> OUT, int64_t n, int beta_on, float alpha, int upper) {
-    constexpr int kMaxQ = 32, KC = 16;
+    constexpr int kMaxQ = 32;
     __shared__ __align__(16) float cs[P * kMaxQ];
     const int Q = OUT.cols();
     for (int e = threadIdx.x; e < P * Q; e += blockDim.x) {
@@ -533,58 +536,89 @@ k_update_f32(MB<const float> X, const float* __restrict__ C, int ldc, int c_row0
     }
     __syncthreads();
     const int nq4 = Q / 4;
-    for (int64_t row = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; row < n;
-         row += (int64_t)gridDim.x * blockDim.x) {
-        float4 acc[kMaxQ / 4];
+    const int64_t total = n * nq4;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t row = e / nq4;
+        const int q0 = (int)(e - row * nq4) * 4;
+        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-        for (int q4 = 0; q4 < kMaxQ / 4; ++q4) acc[q4] = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int k = 0; k < P; k += 4) {
+            const int b = k / X.w;
+            const float4 xv = *reinterpret_cast<const float4*>(X.blk(b) + row * X.w + (k - b * X.w));
+            const float xs[4] = {xv.x, xv.y, xv.z, xv.w};
 #pragma unroll
-        for (int k0 = 0; k0 < P; k0 += (P < KC ? P : KC)) {
-            constexpr int KK = P < KC ? P : KC;
-            float x[KK];
+            for (int kk = 0; kk < 4; ++kk) {
+                const float4 c = *reinterpret_cast<const float4*>(cs + (k + kk) * kMaxQ + q0);
+                acc.x += xs[kk] * c.x;
+                acc.y += xs[kk] * c.y;
+                acc.z += xs[kk] * c.z;
+                acc.w += xs[kk] * c.w;
+            }
+        }
+        float4 y = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (beta_on) {
+            const int by = q0 / Y.w;
+            y = *reinterpret_cast<const float4*>(Y.blk(by) + row * Y.w + (q0 - by * Y.w));
+        }
+        const int bo = q0 / OUT.w;
+        float4 o;
+        o.x = y.x + alpha * acc.x;
+        o.y = y.y + alpha * acc.y;
+        o.z = y.z + alpha * acc.z;
+        o.w = y.w + alpha * acc.w;
+        *reinterpret_cast<float4*>(OUT.blk(bo) + row * OUT.w + (q0 - bo * OUT.w)) = o;
+    }
+    (void)upper;
+}
+
+// In-place triangular form W <- W R^{-1} (P = Q <= 32): the Q/4 threads of a row are
+// consecutive lanes of one warp (32 is a multiple of Q/4), so each thread loads the whole
+// row of X into registers, the warp synchronises, and only then writes its 4 outputs.  The
+// loop runs over whole warps so that every lane reaches the __syncwarp.
+template <int P>
+__global__ void __launch_bounds__(256)
+k_rmul_f32(MB<float> X, const float* __restrict__ R, int ldr, int64_t n) {
+    __shared__ __align__(16) float cs[P * P];
+    for (int e = threadIdx.x; e < P * P; e += blockDim.x) {
+        const int k = e / P, q = e - k * P;
+        cs[e] = R[(int64_t)k * ldr + q];
+    }
+    __syncthreads();
+    constexpr int nq4 = P / 4;
+    static_assert(32 % nq4 == 0, "a row's threads must share a warp");
+    const int64_t total = n * nq4;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t span = (total + 31) / 32 * 32;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < span; e += stride) {
+        const bool live = e < total;
+        const int64_t row = live ? e / nq4 : 0;
+        const int q0 = live ? (int)(e - row * nq4) * 4 : 0;
+        float x[P];
+        if (live) {
 #pragma unroll
-            for (int k4 = 0; k4 < KK / 4; ++k4) {
-                const int k = k0 + k4 * 4, b = k / X.w;
+            for (int k = 0; k < P; k += 4) {
+                const int b = k / X.w;
                 const float4 v =
                     *reinterpret_cast<const float4*>(X.blk(b) + row * X.w + (k - b * X.w));
-                x[k4 * 4] = v.x;
-                x[k4 * 4 + 1] = v.y;
-                x[k4 * 4 + 2] = v.z;
-                x[k4 * 4 + 3] = v.w;
-            }
-#pragma unroll
-            for (int q4 = 0; q4 < kMaxQ / 4; ++q4) {
-                if (q4 < nq4 && (!upper || k0 <= q4 * 4 + 3)) {
-#pragma unroll
-                    for (int kk = 0; kk < KK; ++kk) {
-                        const float4 c =
-                            *reinterpret_cast<const float4*>(cs + (k0 + kk) * kMaxQ + q4 * 4);
-                        acc[q4].x += x[kk] * c.x;
-                        acc[q4].y += x[kk] * c.y;
-                        acc[q4].z += x[kk] * c.z;
-                        acc[q4].w += x[kk] * c.w;
-                    }
-                }
+                x[k] = v.x; x[k + 1] = v.y; x[k + 2] = v.z; x[k + 3] = v.w;
             }
         }
+        __syncwarp();
+        if (live) {
+            float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-        for (int q4 = 0; q4 < kMaxQ / 4; ++q4) {
-            if (q4 < nq4) {
-                const int q0 = q4 * 4;
-                float4 y = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (beta_on) {
-                    const int by = q0 / Y.w;
-                    y = *reinterpret_cast<const float4*>(Y.blk(by) + row * Y.w + (q0 - by * Y.w));
-                }
-                const int bo = q0 / OUT.w;
-                float4 o;
-                o.x = y.x + alpha * acc[q4].x;
-                o.y = y.y + alpha * acc[q4].y;
-                o.z = y.z + alpha * acc[q4].z;
-                o.w = y.w + alpha * acc[q4].w;
-                *reinterpret_cast<float4*>(OUT.blk(bo) + row * OUT.w + (q0 - bo * OUT.w)) = o;
+            for (int k = 0; k < P; ++k) {
+                const float4 c = *reinterpret_cast<const float4*>(cs + k * P + q0);
+                acc.x += x[k] * c.x;
+                acc.y += x[k] * c.y;
+                acc.z += x[k] * c.z;
+                acc.w += x[k] * c.w;
             }
+            const int bo = q0 / X.w;
+            *reinterpret_cast<float4*>(X.blk(bo) + row * X.w + (q0 - bo * X.w)) = acc;
         }
+        __syncwarp();
     }
 }
 
