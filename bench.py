@@ -112,6 +112,21 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def measured_traffic(kernel_class):
+    """DRAM bytes per algorithmic byte of a kernel class from the committed ncu record
+    (profiles/dominant_kernel_traffic.json), valid only while the kernel source it was
+    captured from is unchanged (sha256 of csrc/kernels.cuh)."""
+    import hashlib
+    try:
+        rec = json.load(open(os.path.join(ROOT, "profiles", "dominant_kernel_traffic.json")))
+        src = open(os.path.join(ROOT, "paper_1804_10629_gb300", "csrc", "kernels.cuh"), "rb").read()
+        if rec.get("kernels_cuh_sha256") != hashlib.sha256(src).hexdigest():
+            return None
+        return rec.get("classes", {}).get(kernel_class)
+    except Exception:
+        return None
+
+
 def roofline_and_table(prof, args):
     """Roofline of the dominant kernel class (by device time) and the per-class table.
     float64: FP64 ALU bound (alu) for the arithmetic kernels; otherwise the HBM bound."""
@@ -124,11 +139,14 @@ def roofline_and_table(prof, args):
         if args.precision == "fp64" and name in ("gram", "block_update", "spmm", "chol_inv",
                                                    "xr_update", "gram_reduce"):
             ach = d["flops"] / sec / 1e12
+            ratio = measured_traffic(name)
+            traffic = (ratio * d["bytes"] / max(d["launches"], 1)) if ratio else None
             roof = {"kernel": name, "bound": "alu", "achieved": ach,
                     "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS,
                     "peak_source": "derived FP64 FMA rate: 152 SMs x 2 DFMA/clk x 2 x 2.07 GHz",
-                    "traffic": None, "launches": d["launches"],
-                    "avg_launch_ms": d["ms"] / max(d["launches"], 1)}
+                    "traffic": traffic, "algorithmic_bytes_per_launch":
+                        d["bytes"] / max(d["launches"], 1),
+                    "launches": d["launches"], "avg_launch_ms": d["ms"] / max(d["launches"], 1)}
         else:
             peak = hbm or HBM_FALLBACK_GBS
             ach = d["bytes"] / sec / 1e9
