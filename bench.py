@@ -165,25 +165,46 @@ def roofline_and_table(prof, args):
     return roof, table
 
 
-def timed_solves(args, S, b, x, s, stream, dist, clocks):
+class CudaTimer:
+    """Device time between two CUDA events recorded on the solve stream."""
+
+    def __init__(self, stream):
+        import torch
+        self.stream = stream
+        self.sync = torch.cuda.synchronize
+        self.ev0 = torch.cuda.Event(enable_timing=True)
+        self.ev1 = torch.cuda.Event(enable_timing=True)
+        self.device = "cuda"
+
+    def start(self):
+        self.ev0.record(self.stream)
+
+    def stop(self):
+        self.ev1.record(self.stream)
+
+    def ms(self):
+        return self.ev0.elapsed_time(self.ev1)
+
+
+def timed_solves(args, S, b, x, s, stream, dist, clocks, timer=None):
     """W warm-up solves, then K timed solves bracketed by barrier + synchronize, CUDA events
-    on the solve stream; per-kernel-class accounting summed over the timed solves."""
+    on the solve stream; per-kernel-class accounting summed over the timed solves; the step
+    time is the maximum over ranks."""
     import torch
+    timer = timer or CudaTimer(stream)
     its = []
     st = 0
     for _ in range(args.warmup):
         _, it, _, st = S.solve(b, s=s, tol=args.tol, maxit=args.maxit, x=x)
         its.append(it)
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
     launches = 0
     prof = {}
     if dist:
         dist.barrier()
-    torch.cuda.synchronize()
+    timer.sync()
     if clocks:
         clocks.start()
-    ev0.record(stream)
+    timer.start()
     for _ in range(args.steps):
         _, it, hist, st = S.solve(b, s=s, tol=args.tol, maxit=args.maxit, x=x)
         its.append(it)
@@ -192,14 +213,14 @@ def timed_solves(args, S, b, x, s, stream, dist, clocks):
             agg = prof.setdefault(k, {"ms": 0.0, "launches": 0, "flops": 0.0, "bytes": 0.0})
             for f in agg:
                 agg[f] += v[f]
-    ev1.record(stream)
-    torch.cuda.synchronize()
+    timer.stop()
+    timer.sync()
     ck = clocks.stop() if clocks else None
     if dist:
         dist.barrier()
-    ms = ev0.elapsed_time(ev1) / args.steps
+    ms = timer.ms() / args.steps
     if dist:
-        tt = torch.tensor([ms], device="cuda")
+        tt = torch.tensor([ms], device=timer.device)
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         ms = float(tt.item())
     return {"ms": ms, "iters": its[-1], "status": st, "launches": launches, "prof": prof,
