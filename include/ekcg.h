@@ -206,9 +206,12 @@ int ekcg_permute(ekcg_ctx* ctx, const double* x, double* y, int direction);
 
 /* ---- batched solves: many independent systems in one persistent launch ----------- */
 /* Not in the paper: the s-step SRE-CG of Algorithm 4 (A-CholQR, fresh-product CGS2) run on
- * nsys independent SPD systems at once.  One CTA solves one system at a time, taking
+ * nsys independent SPD systems at once.  A group of CTAs -- one CTA, or a thread-block
+ * cluster of 2, 4 or 8 CTAs that split the system's rows and reduce their block inner
+ * products through distributed shared memory -- solves one system at a time, taking
  * systems from a device queue, largest first; the gather, the solve and the scatter are one
- * captured CUDA graph replayed per call.                                                   */
+ * captured CUDA graph replayed per call.  Results are deterministic for a given launch
+ * shape; different cluster sizes sum the inner products in different orders.             */
 typedef struct ekcg_batch ekcg_batch;
 
 /* n[nsys]: system sizes.  rowptr: the nsys local row-pointer arrays (n_k + 1 entries each,
@@ -229,12 +232,21 @@ int ekcg_batched_setup(int nsys, const int64_t* n, const int64_t* rowptr, const 
 int ekcg_batched_solve(ekcg_batch* batch, const double* b, int s, double tol, int maxit,
                        double* x, int* iters, int* status);
 
-/* Time three launch shapes (threads per CTA x CTAs per SM) on right-hand side b and keep
- * the fastest for later solves.                                                          */
+/* Time seven launch shapes (threads per CTA x CTAs per SM x CTAs per system) with one solve
+ * each on right-hand side b (device array, as in ekcg_batched_solve; a small maxit keeps
+ * this short) and keep the fastest for later solves.  Errors: EKCG_EINVAL, EKCG_ECUDA.    */
 int ekcg_batched_tune(ekcg_batch* batch, const double* b, int s, double tol, int maxit);
 
-/* Launch shape in use and device time (ms) of the last captured solve.                   */
-int ekcg_batched_info(const ekcg_batch* batch, int* threads, int* ctas_per_sm, double* last_ms);
+/* Set the launch shape: threads per CTA in {256, 512}, CTAs per SM in {1, 2}, CTAs per
+ * system (cluster) in {1, 2, 4, 8}; setup chooses 512 x 1 x 4.  The persistent grid holds
+ * as many groups as the GPU keeps resident at once.  Errors: EKCG_EINVAL (values outside
+ * these sets, or a shape with no resident group), EKCG_ECUDA.                            */
+int ekcg_batched_set_shape(ekcg_batch* batch, int threads, int ctas_per_sm, int cluster);
+
+/* Launch shape in use (threads per CTA, CTAs per SM, CTAs per system, groups launched) and
+ * device time (ms) of the last captured solve; every pointer nullable.                   */
+int ekcg_batched_info(const ekcg_batch* batch, int* threads, int* ctas_per_sm, int* cluster,
+                      int* groups, double* last_ms);
 
 /* Release the batch and its device memory (NULL accepted).                               */
 void ekcg_batched_destroy(ekcg_batch* batch);

@@ -1,11 +1,16 @@
 // Batched s-step SRE-CG (Algorithm 4) for many independent systems in one persistent launch.
 //
-// Each CTA takes the next system from a device work queue (systems are queued largest
-// first) and runs the whole s-step loop for it with CTA-wide barriers only: no CTA ever
-// waits on another, and every loop is bounded by maxit.  The steps are the same as the
+// A group of CTAs -- one CTA, or the CTAs of one thread-block cluster -- takes the next
+// system from a device work queue (systems are queued largest first) and runs the whole
+// s-step loop for it.  Each CTA of the group owns a contiguous range of the system's rows;
+// block inner products are reduced across the cluster through distributed shared memory,
+// summed in rank order by every CTA, so that all CTAs hold bit-identical Gram matrices,
+// Cholesky factors and residual norms and take the same branches.  Groups never wait on
+// one another, and every loop is bounded by maxit.  The steps are the same as the
 // single-system path (T(r_0), sparse products, CGS2 with fresh products against the two
-// previous blocks, A-CholQR, alpha = V^T r, x/r update), written as CTA-cooperative device
-// functions.  Precision: float64, or float32 inner solves in a float64 refinement loop.
+// previous blocks, A-CholQR, alpha = V^T r, x/r update).  Precision: float64, or float32
+// inner solves in a float64 refinement loop.
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -34,6 +39,11 @@ constexpr int kMaxT = 16;              // t <= 16
 constexpr int kMaxS = 4;               // s <= 4
 constexpr int kMaxP = 2 * kMaxT;       // window of two blocks
 constexpr int kMaxST = kMaxS * kMaxT;
+constexpr int kPart = kMaxP * kMaxT;   // largest reduced array (>= kMaxST)
+constexpr int kMaxCluster = 8;         // portable cluster size
+constexpr int kDefaultCluster = 4;     // CTAs per system unless set or tuned otherwise
+
+namespace cg = cooperative_groups;
 
 struct Sys {
     int64_t n;        // rows
@@ -65,7 +75,49 @@ struct Params {
     double* rho_out;            // per system: final recursive (or refined) residual norm
 };
 
-// ---- CTA-wide building blocks ---------------------------------------------------------
+// ---- group-wide building blocks -------------------------------------------------------
+
+// The CTAs that solve one system: a single CTA (CL = false; barriers are __syncthreads) or
+// the CTAs of one thread-block cluster (CL = true; barriers are cluster barriers, whose
+// release/acquire semantics also order one CTA's global-memory writes before another CTA's
+// reads).  CTA `rank` owns rows [lo, hi) of the system.
+template <bool CL>
+struct Grp {
+    int rank = 0, size = 1;
+    int64_t lo = 0, hi = 0;
+    double* part = nullptr;   // 2 x kPart doubles of shared memory: this CTA's partial sums
+    int flip = 0;
+    __device__ void rows(int64_t n) {
+        lo = n * rank / size;
+        hi = n * (rank + 1) / size;
+    }
+    __device__ void sync() {
+        if constexpr (CL)
+            cg::this_cluster().sync();
+        else
+            __syncthreads();
+    }
+    // this CTA's partial-sum buffer for the next reduction
+    __device__ double* buf() { return part + flip * kPart; }
+    // out[i] = sum over the group's CTAs, in rank order, of their buf()[i] (i < m); every CTA
+    // forms the same sums.  The two buffers alternate, so one barrier per reduction is
+    // enough: a CTA writes a buffer again only after passing the next reduction's barrier,
+    // which every CTA reaches after reading the buffer.
+    __device__ void reduce(double* out, int m) {
+        if constexpr (CL) {
+            sync();
+            cg::cluster_group cl = cg::this_cluster();
+            double* mine = buf();
+            for (int i = threadIdx.x; i < m; i += blockDim.x) {
+                double s = 0.0;
+                for (int c = 0; c < size; ++c) s += cl.map_shared_rank(mine, c)[i];
+                out[i] = s;
+            }
+            flip ^= 1;
+            __syncthreads();
+        }
+    }
+};
 
 __device__ double cta_sum(double v, double* red) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -82,14 +134,39 @@ __device__ double cta_sum(double v, double* red) {
     return red[32];
 }
 
-template <typename T>
-__device__ void cta_spmm(T* __restrict__ U, const T* __restrict__ W, const int32_t* rp,
-                         const int32_t* col, const T* val, int64_t n, int t) {
-    for (int64_t e = threadIdx.x; e < n * t; e += blockDim.x) {
+// Sum of v over the group (red: >= 34 doubles of shared memory).
+template <bool CL>
+__device__ double grp_sum(Grp<CL>& g, double v, double* red) {
+    const double local = cta_sum(v, red);
+    if constexpr (!CL) {
+        return local;
+    } else {
+        if (threadIdx.x == 0) g.buf()[0] = local;
+        g.reduce(red + 33, 1);
+        return red[33];
+    }
+}
+
+// Load of a vector entry that another CTA of the cluster may have written in this launch:
+// taken from L2 (ld.global.cg), so it never depends on a line cached in this SM's L1.
+template <bool CL, typename T>
+__device__ __forceinline__ T ld_group(const T* p) {
+    if constexpr (CL)
+        return __ldcg(p);
+    else
+        return *p;
+}
+
+// U = A W on this CTA's rows (W is read at any row of the system).
+template <typename T, bool CL>
+__device__ void grp_spmm(const Grp<CL>& g, T* U, const T* W, const int32_t* __restrict__ rp,
+                         const int32_t* __restrict__ col, const T* __restrict__ val, int t) {
+    for (int64_t e = g.lo * t + threadIdx.x; e < g.hi * t; e += blockDim.x) {
         const int64_t i = e / t;
         const int c = (int)(e - i * t);
         T acc = T(0);
-        for (int j = rp[i]; j < rp[i + 1]; ++j) acc += val[j] * W[(int64_t)col[j] * t + c];
+        for (int j = rp[i]; j < rp[i + 1]; ++j)
+            acc += val[j] * ld_group<CL>(W + (int64_t)col[j] * t + c);
         U[e] = acc;
     }
 }
@@ -121,14 +198,17 @@ struct CtaAcc<float, double> {
     __device__ __forceinline__ double value() const { return a.value(); }
 };
 
-// C[p*Q + q] = sum_rows X_p[row] Y_q[row] (accumulated in Acc, stored as double); X is nx
-// blocks (n x t), Y is ny blocks of ty columns.  With fewer outputs than threads, each output
-// is split over row stripes reduced in stripe order (deterministic).
-template <typename T, typename Acc>
-__device__ void cta_gram(double* C, const T* const* X, int nx, const T* const* Y, int ny, int ty,
-                         int64_t n, int t, double* scratch /* >= blockDim.x */) {
+// C[p*Q + q] = sum over the system's rows of X_p[row] Y_q[row] (accumulated in Acc, stored as
+// double); X is nx blocks (n x t), Y is ny blocks of ty columns.  Each CTA sums its own rows;
+// with fewer outputs than threads, each output is split over row stripes reduced in stripe
+// order; the group's partials are then reduced in rank order (deterministic).
+template <typename T, typename Acc, bool CL>
+__device__ void grp_gram(Grp<CL>& g, double* C, const T* const* X, int nx, const T* const* Y,
+                         int ny, int ty, int t, double* scratch /* >= blockDim.x */) {
     const int P = nx * t, Q = ny * ty, PQ = P * Q;
     const int tid = threadIdx.x;
+    const int64_t lo = g.lo, hi = g.hi;
+    double* dst = CL ? g.buf() : C;
     if (PQ * 2 > (int)blockDim.x) {
         for (int o = tid; o < PQ; o += blockDim.x) {
             const int p = o / Q, q = o - p * Q;
@@ -136,40 +216,42 @@ __device__ void cta_gram(double* C, const T* const* X, int nx, const T* const* Y
             const T* yb = Y[q / ty];
             const int xc = p % t, yc = q % ty;
             CtaAcc<T, Acc> acc;
-            for (int64_t row = 0; row < n; ++row) acc.add(xb[row * t + xc], yb[row * ty + yc]);
-            C[o] = acc.value();
+            for (int64_t row = lo; row < hi; ++row) acc.add(xb[row * t + xc], yb[row * ty + yc]);
+            dst[o] = acc.value();
         }
         __syncthreads();
-        return;
+    } else {
+        const int stripes = (int)blockDim.x / PQ;
+        CtaAcc<T, Acc> acc;
+        const bool active = tid < PQ * stripes;
+        if (active) {
+            const int o = tid % PQ, st = tid / PQ;
+            const int p = o / Q, q = o - p * Q;
+            const T* xb = X[p / t];
+            const T* yb = Y[q / ty];
+            const int xc = p % t, yc = q % ty;
+            for (int64_t row = lo + st; row < hi; row += stripes)
+                acc.add(xb[row * t + xc], yb[row * ty + yc]);
+        }
+        __syncthreads();
+        if (active) scratch[tid] = acc.value();
+        __syncthreads();
+        for (int o = tid; o < PQ; o += blockDim.x) {
+            double s = 0.0;
+            for (int k = 0; k < stripes; ++k) s += scratch[k * PQ + o];
+            dst[o] = s;
+        }
+        __syncthreads();
     }
-    const int stripes = (int)blockDim.x / PQ;
-    CtaAcc<T, Acc> acc;
-    const bool active = tid < PQ * stripes;
-    if (active) {
-        const int o = tid % PQ, st = tid / PQ;
-        const int p = o / Q, q = o - p * Q;
-        const T* xb = X[p / t];
-        const T* yb = Y[q / ty];
-        const int xc = p % t, yc = q % ty;
-        for (int64_t row = st; row < n; row += stripes) acc.add(xb[row * t + xc], yb[row * ty + yc]);
-    }
-    __syncthreads();
-    if (active) scratch[tid] = acc.value();
-    __syncthreads();
-    for (int o = tid; o < PQ; o += blockDim.x) {
-        double s = 0.0;
-        for (int k = 0; k < stripes; ++k) s += scratch[k * PQ + o];
-        C[o] = s;
-    }
-    __syncthreads();
+    g.reduce(C, PQ);
 }
 
-// OUT = Y - sum_b X_b C_b  (C: (nx t) x t), OUT may alias Y.
-template <typename T, typename CT>
-__device__ void cta_sub(T* OUT, const T* Y, const T* const* X, int nx, const CT* C, int64_t n,
-                        int t) {
+// OUT = Y - sum_b X_b C_b on this CTA's rows (C: (nx t) x t); OUT may alias Y.
+template <typename T, typename CT, bool CL>
+__device__ void grp_sub(const Grp<CL>& g, T* OUT, const T* Y, const T* const* X, int nx,
+                        const CT* C, int t) {
     const int P = nx * t;
-    for (int64_t e = threadIdx.x; e < n * t; e += blockDim.x) {
+    for (int64_t e = g.lo * t + threadIdx.x; e < g.hi * t; e += blockDim.x) {
         const int64_t i = e / t;
         const int q = (int)(e - i * t);
         CT acc = CT(0);
@@ -179,10 +261,10 @@ __device__ void cta_sub(T* OUT, const T* Y, const T* const* X, int nx, const CT*
     __syncthreads();
 }
 
-// W <- W Rinv (Rinv t x t upper triangular, in place), arithmetic in T.
-template <typename T>
-__device__ void cta_rmul(T* W, const T* Rinv, int64_t n, int t) {
-    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+// W <- W Rinv on this CTA's rows (Rinv t x t upper triangular, in place), arithmetic in T.
+template <typename T, bool CL>
+__device__ void grp_rmul(const Grp<CL>& g, T* W, const T* Rinv, int t) {
+    for (int64_t i = g.lo + threadIdx.x; i < g.hi; i += blockDim.x) {
         T row[kMaxT];
         for (int c = 0; c < t; ++c) row[c] = W[i * t + c];
         for (int q = 0; q < t; ++q) {
@@ -203,6 +285,7 @@ __device__ const T* cta_cast(const double* src, T* dst, int m) {
 }
 
 // Upper Cholesky of the t x t matrix G (upper triangle), R^{-1}; thread 0 only (t <= 16).
+// Every CTA of a group factors the same G (bit-identical after the rank-order reduction).
 // Returns 1 on breakdown (pivot d_i <= tol*|G_ii| or non-finite).
 __device__ int cta_chol(const double* G, double* Rinv, double* S, double* R, int t, double tol,
                         int* flag_sh) {
@@ -250,17 +333,18 @@ struct Shared {
     float Rinvf[kMaxT * kMaxT];
     double alpha[kMaxST];
     double red[40];
+    double part[2 * kPart];       // cluster partial sums (two alternating buffers)
     int flag;
 };
 
 // s-step SRE-CG on one system in precision T: x (T) from its content, r (T) = residual.
 // Returns the number of iterations; *st receives OK / MAXIT / BREAKDOWN; *rho the final
-// recursive residual norm.
+// recursive residual norm.  Every CTA of the group returns the same values.
 // stag > 0: stop when no new minimum of rho was reached in the last `stag` iterations.
-template <typename T>
-__device__ int cta_sstep(const Params& P, const Sys& S, T* x, T* r, T* Wb, T* Zb, const T* val,
-                         double rho0, double tol_abs, int maxit, Shared& sh, double* scratch,
-                         int* st, double* rho_out, int stag = 0) {
+template <typename T, bool CL>
+__device__ int cta_sstep(const Params& P, const Sys& S, Grp<CL>& g, T* x, T* r, T* Wb, T* Zb,
+                         const T* val, double rho0, double tol_abs, int maxit, Shared& sh,
+                         double* scratch, int* st, double* rho_out, int stag = 0) {
     const int t = P.t, s = P.s;
     const int64_t n = S.n, slot = n * t;
     const int32_t* rp = P.rowptr + S.rp0;
@@ -280,37 +364,39 @@ __device__ int cta_sstep(const Params& P, const Sys& S, T* x, T* r, T* Wb, T* Zb
             const int64_t j = j0 + i;
             if (j == 0) {
                 T* w = W(0);
-                for (int64_t e = threadIdx.x; e < slot; e += blockDim.x) {
+                for (int64_t e = g.lo * t + threadIdx.x; e < g.hi * t; e += blockDim.x) {
                     const int64_t row = e / t;
                     w[e] = ((int)(e - row * t) == dom[row]) ? r[row] : T(0);
                 }
-                __syncthreads();
-                cta_spmm<T>(Z(0), W(0), rp, col, val, n, t);
+                g.sync();
+                grp_spmm<T>(g, Z(0), W(0), rp, col, val, t);
                 __syncthreads();
             } else {
                 const T* cand = Z(j - 1);
-                cta_spmm<T>(Z(j), cand, rp, col, val, n, t);
+                if constexpr (CL) g.sync();   // Z(j-1) complete on every CTA's rows
+                grp_spmm<T>(g, Z(j), cand, rp, col, val, t);
                 __syncthreads();
                 const int64_t q0 = j >= 2 ? j - 2 : 0;
                 const int qc = (int)(j - q0);
                 const T* Q[2] = {W(q0), W(q0 + 1)};
                 for (int pass = 0; pass < 2; ++pass) {
                     const T* Zs[1] = {Z(j)};
-                    cta_gram<T, T>(sh.C, Q, qc, Zs, 1, t, n, t, scratch);
+                    grp_gram<T, T>(g, sh.C, Q, qc, Zs, 1, t, t, scratch);
                     if constexpr (sizeof(T) == sizeof(double)) {
-                        cta_sub<T, double>(W(j), pass == 0 ? cand : W(j), Q, qc, sh.C, n, t);
+                        grp_sub<T, double>(g, W(j), pass == 0 ? cand : W(j), Q, qc, sh.C, t);
                     } else {
                         const float* Cf = cta_cast<float>(sh.C, sh.Cf, qc * t * t);
-                        cta_sub<T, float>(W(j), pass == 0 ? cand : W(j), Q, qc, Cf, n, t);
+                        grp_sub<T, float>(g, W(j), pass == 0 ? cand : W(j), Q, qc, Cf, t);
                     }
-                    cta_spmm<T>(Z(j), W(j), rp, col, val, n, t);
+                    if constexpr (CL) g.sync();   // W(j) complete on every CTA's rows
+                    grp_spmm<T>(g, Z(j), W(j), rp, col, val, t);
                     __syncthreads();
                 }
             }
             // A-CholQR
             const T* Wj[1] = {W(j)};
             const T* Zj[1] = {Z(j)};
-            cta_gram<T, double>(sh.G, Wj, 1, Zj, 1, t, n, t, scratch);
+            grp_gram<T, double>(g, sh.G, Wj, 1, Zj, 1, t, t, scratch);
             if (cta_chol(sh.G, sh.Rinv, sh.S, sh.R, t, P.bd_tol, &sh.flag)) {
                 *st = EKCG_EBREAKDOWN;
                 *rho_out = rho;
@@ -321,8 +407,8 @@ __device__ int cta_sstep(const Params& P, const Sys& S, T* x, T* r, T* Wb, T* Zb
                 Ri = (const T*)sh.Rinv;
             else
                 Ri = (const T*)cta_cast<float>(sh.Rinv, sh.Rinvf, t * t);
-            cta_rmul<T>(W(j), Ri, n, t);
-            cta_rmul<T>(Z(j), Ri, n, t);
+            grp_rmul<T>(g, W(j), Ri, t);
+            grp_rmul<T>(g, Z(j), Ri, t);
         }
         nb = j0 + s;
         // alpha = V^T r; x += V alpha; r -= (A V) alpha
@@ -333,9 +419,9 @@ __device__ int cta_sstep(const Params& P, const Sys& S, T* x, T* r, T* Wb, T* Zb
             AVs[i] = Z(j0 + i);
         }
         const T* rv[1] = {r};
-        cta_gram<T, double>(sh.alpha, Vs, s, rv, 1, 1, n, t, scratch);
+        grp_gram<T, double>(g, sh.alpha, Vs, s, rv, 1, 1, t, scratch);
         double local = 0.0;
-        for (int64_t row = threadIdx.x; row < n; row += blockDim.x) {
+        for (int64_t row = g.lo + threadIdx.x; row < g.hi; row += blockDim.x) {
             double sx = 0.0, sr = 0.0;
             for (int b = 0; b < s; ++b)
                 for (int c = 0; c < t; ++c) {
@@ -348,7 +434,7 @@ __device__ int cta_sstep(const Params& P, const Sys& S, T* x, T* r, T* Wb, T* Zb
             r[row] = ri;
             local += (double)ri * (double)ri;
         }
-        rho = sqrt(cta_sum(local, sh.red));
+        rho = sqrt(grp_sum(g, local, sh.red));
         if (rho < best) {
             best = rho;
             k_best = k;
@@ -360,7 +446,10 @@ __device__ int cta_sstep(const Params& P, const Sys& S, T* x, T* r, T* Wb, T* Zb
     return k - 1;
 }
 
-__device__ double cta_residual64(const Params& P, const Sys& S, double* r) {
+// r = b - A x (float64) on this CTA's rows; returns ||r|| over the system.  x is read at any
+// row, so every CTA's x must be complete (a group barrier) before the call.
+template <bool CL>
+__device__ double cta_residual64(Grp<CL>& g, const Params& P, const Sys& S, double* r) {
     const int32_t* rp = P.rowptr + S.rp0;
     const int32_t* col = P.col + S.nz0;
     const double* val = P.val + S.nz0;
@@ -368,32 +457,52 @@ __device__ double cta_residual64(const Params& P, const Sys& S, double* r) {
     const double* x = P.x + S.row0;
     __shared__ double red[40];
     double local = 0.0;
-    for (int64_t i = threadIdx.x; i < S.n; i += blockDim.x) {
+    for (int64_t i = g.lo + threadIdx.x; i < g.hi; i += blockDim.x) {
         double acc = 0.0;
-        for (int j = rp[i]; j < rp[i + 1]; ++j) acc += val[j] * x[col[j]];
+        for (int j = rp[i]; j < rp[i + 1]; ++j) acc += val[j] * ld_group<CL>(x + col[j]);
         const double ri = b[i] - acc;
         r[i] = ri;
         local += ri * ri;
     }
-    return sqrt(cta_sum(local, red));
+    return sqrt(grp_sum(g, local, red));
 }
 
-template <bool MIXED>
+template <bool MIXED, bool CL>
 __global__ void __launch_bounds__(512) k_batched(Params P) {
     __shared__ Shared sh;
-    __shared__ int sid;
+    __shared__ int sid_sh;
     extern __shared__ double scratch[];
+    Grp<CL> g;
+    g.part = sh.part;
+    if constexpr (CL) {
+        g.rank = (int)cg::this_cluster().block_rank();
+        g.size = (int)cg::this_cluster().num_blocks();
+    }
     while (true) {
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            const int q = atomicAdd(P.queue, 1);
-            sid = q < P.nsys ? P.order[q] : -1;
+        int sid;
+        if constexpr (CL) {
+            // rank 0 takes the next system; the others read its choice from its shared memory
+            if (g.rank == 0 && threadIdx.x == 0) {
+                const int q = atomicAdd(P.queue, 1);
+                sid_sh = q < P.nsys ? P.order[q] : -1;
+            }
+            g.sync();
+            sid = *cg::this_cluster().map_shared_rank(&sid_sh, 0);
+            g.sync();   // read by every CTA before rank 0 exits or takes the next system
+        } else {
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                const int q = atomicAdd(P.queue, 1);
+                sid_sh = q < P.nsys ? P.order[q] : -1;
+            }
+            __syncthreads();
+            sid = sid_sh;
         }
-        __syncthreads();
         if (sid < 0) return;
         const Sys S = P.sys[sid];
+        g.rows(S.n);
         double* r64 = P.r64 + S.row0;
-        const double rho0 = cta_residual64(P, S, r64);
+        const double rho0 = cta_residual64(g, P, S, r64);
         int its = 0, st = EKCG_OK;
         double rho = rho0;
         if (!isfinite(rho0)) {
@@ -402,7 +511,7 @@ __global__ void __launch_bounds__(512) k_batched(Params P) {
             double* Wb = (double*)P.ws + S.ws0;
             double* Zb = Wb + (int64_t)(P.s + 2) * S.n * P.t;
             double* xx = P.x + S.row0;
-            its = cta_sstep<double>(P, S, xx, r64, Wb, Zb, P.val + S.nz0, rho0, P.tol * rho0,
+            its = cta_sstep<double>(P, S, g, xx, r64, Wb, Zb, P.val + S.nz0, rho0, P.tol * rho0,
                                     P.maxit, sh, scratch, &st, &rho);
         } else if (rho0 > 0) {
             float* Wb = (float*)P.ws + S.ws0;
@@ -412,7 +521,7 @@ __global__ void __launch_bounds__(512) k_batched(Params P) {
             st = EKCG_MAXIT;
             for (int ref = 0; ref < P.max_refine && its < P.maxit; ++ref) {
                 const double sc = 1.0 / rho;
-                for (int64_t i = threadIdx.x; i < S.n; i += blockDim.x) {
+                for (int64_t i = g.lo + threadIdx.x; i < g.hi; i += blockDim.x) {
                     r32[i] = (float)(r64[i] * sc);
                     d[i] = 0.f;
                 }
@@ -421,13 +530,13 @@ __global__ void __launch_bounds__(512) k_batched(Params P) {
                 double irho = 0;
                 // the inner solve reduces r only as far as the outer tolerance still needs
                 const double itol = fmax(P.inner_tol, 0.5 * P.tol * rho0 / rho);
-                its += cta_sstep<float>(P, S, d, r32, Wb, Zb, P.val32 + S.nz0, 1.0, itol,
+                its += cta_sstep<float>(P, S, g, d, r32, Wb, Zb, P.val32 + S.nz0, 1.0, itol,
                                         P.maxit - its, sh, scratch, &ist, &irho, 50);
-                for (int64_t i = threadIdx.x; i < S.n; i += blockDim.x)
+                for (int64_t i = g.lo + threadIdx.x; i < g.hi; i += blockDim.x)
                     P.x[S.row0 + i] += rho * (double)d[i];
-                __syncthreads();
+                g.sync();   // the residual reads x on every CTA's rows
                 const double rho_prev = rho;
-                rho = cta_residual64(P, S, r64);
+                rho = cta_residual64(g, P, S, r64);
                 if (!(rho > P.tol * rho0)) {
                     st = EKCG_OK;
                     break;
@@ -439,7 +548,7 @@ __global__ void __launch_bounds__(512) k_batched(Params P) {
                 if (rho > 0.9 * rho_prev) break;   // refinement stagnated: EKCG_MAXIT
             }
         }
-        if (threadIdx.x == 0) {
+        if (g.rank == 0 && threadIdx.x == 0) {
             P.iters[sid] = its;
             P.status[sid] = st;
             P.rho_out[sid] = rho;
@@ -478,6 +587,8 @@ struct ekcg_batch {
     int *d_iters = nullptr, *d_status = nullptr;
     double* d_rho = nullptr;
     int threads = 512, ctas_per_sm = 1;
+    int cluster = 1;            // CTAs per system (a thread-block cluster when > 1)
+    int groups = 0;             // persistent groups launched (CTAs / cluster)
     // captured graph of one solve
     cudaGraphExec_t graph = nullptr;
     int g_s = -1, g_maxit = -1;
@@ -512,15 +623,85 @@ int launch_solve(ekcg_batch* B, int s, double tol, int maxit) {
     P.iters = B->d_iters;
     P.status = B->d_status;
     P.rho_out = B->d_rho;
-    const int grid = std::min(B->nsys, B->num_sms * B->ctas_per_sm);
     const size_t smem = (size_t)B->threads * sizeof(double);
     EB_CUDA(cudaMemsetAsync(B->d_queue, 0, sizeof(int), B->stream));
     EB_CUDA(cudaMemsetAsync(B->d_x, 0, B->ntot * sizeof(double), B->stream));
-    if (B->precision == EKCG_FP64)
-        k_batched<false><<<grid, B->threads, smem, B->stream>>>(P);
-    else
-        k_batched<true><<<grid, B->threads, smem, B->stream>>>(P);
+    const bool mixed = B->precision != EKCG_FP64;
+    if (B->cluster == 1) {
+        const int grid = B->groups;
+        if (!mixed)
+            k_batched<false, false><<<grid, B->threads, smem, B->stream>>>(P);
+        else
+            k_batched<true, false><<<grid, B->threads, smem, B->stream>>>(P);
+    } else {
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = (unsigned)B->cluster;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.gridDim = dim3((unsigned)(B->groups * B->cluster));
+        cfg.blockDim = dim3((unsigned)B->threads);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = B->stream;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        if (!mixed)
+            EB_CUDA(cudaLaunchKernelEx(&cfg, k_batched<false, true>, P));
+        else
+            EB_CUDA(cudaLaunchKernelEx(&cfg, k_batched<true, true>, P));
+    }
     EB_CUDA(cudaGetLastError());
+    return EKCG_OK;
+}
+
+// Launch shape: `threads` per CTA, `cluster` CTAs per system, at most `ctas_per_sm` CTAs per
+// SM.  The persistent grid holds as many groups as can be resident at once (never more than
+// there are systems), so every group runs from the start; groups never wait on one another.
+int set_shape(ekcg_batch* B, int threads, int ctas_per_sm, int cluster) {
+    if ((threads != 256 && threads != 512) || ctas_per_sm < 1 || ctas_per_sm > 2 ||
+        (cluster != 1 && cluster != 2 && cluster != 4 && cluster != kMaxCluster)) {
+        g_berr = "ekcg_batched_set_shape: threads in {256, 512}, ctas_per_sm in {1, 2}, "
+                 "cluster in {1, 2, 4, 8}";
+        return EKCG_EINVAL;
+    }
+    const bool mixed = B->precision != EKCG_FP64;
+    const size_t smem = (size_t)threads * sizeof(double);
+    int groups = 0;
+    if (cluster == 1) {
+        int per_sm = 0;
+        EB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &per_sm, mixed ? k_batched<true, false> : k_batched<false, false>, threads, smem));
+        groups = B->num_sms * std::min(per_sm, ctas_per_sm);
+    } else {
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = (unsigned)cluster;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.gridDim = dim3((unsigned)(cluster * B->num_sms));
+        cfg.blockDim = dim3((unsigned)threads);
+        cfg.dynamicSmemBytes = smem;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        int nc = 0;
+        EB_CUDA(cudaOccupancyMaxActiveClusters(
+            &nc, (const void*)(mixed ? k_batched<true, true> : k_batched<false, true>), &cfg));
+        groups = std::min(nc, B->num_sms * ctas_per_sm / cluster);
+    }
+    if (groups < 1) {
+        g_berr = "ekcg_batched_set_shape: no resident group of this shape";
+        return EKCG_EINVAL;
+    }
+    B->threads = threads;
+    B->ctas_per_sm = ctas_per_sm;
+    B->cluster = cluster;
+    B->groups = std::min(groups, B->nsys);
+    if (B->graph) {
+        cudaGraphExecDestroy(B->graph);
+        B->graph = nullptr;
+    }
     return EKCG_OK;
 }
 
@@ -681,22 +862,25 @@ int ekcg_batched_setup(int nsys, const int64_t* n, const int64_t* rowptr, const 
     EB_TRY(cudaMemcpy(B->d_perm, hperm.data(), hperm.size() * sizeof(int64_t),
                       cudaMemcpyHostToDevice));
 #undef EB_TRY
+    const int rc = set_shape(B, 512, 1, kDefaultCluster);
+    if (rc != EKCG_OK) return fail(rc);
     *out = B;
     return EKCG_OK;
 }
 
 int ekcg_batched_tune(ekcg_batch* B, const double* b, int s, double tol, int maxit) {
-    if (!B || !b) return EKCG_EINVAL;
-    const int cand_threads[3] = {256, 512, 512};
-    const int cand_ctas[3] = {2, 1, 2};
+    if (!B || !b || s < 1 || s > B->max_s || !(tol > 0) || maxit < 0) return EKCG_EINVAL;
+    constexpr int kCand = 7;
+    const int cand_threads[kCand] = {512, 256, 512, 512, 512, 256, 256};
+    const int cand_ctas[kCand] = {1, 2, 1, 1, 1, 2, 2};
+    const int cand_cluster[kCand] = {1, 1, 2, 4, 8, 4, 8};
     float best = 1e30f;
-    int bt = B->threads, bc = B->ctas_per_sm;
+    int bt = B->threads, bc = B->ctas_per_sm, bk = B->cluster;
     cudaEvent_t e0, e1;
     EB_CUDA(cudaEventCreate(&e0));
     EB_CUDA(cudaEventCreate(&e1));
-    for (int i = 0; i < 3; ++i) {
-        B->threads = cand_threads[i];
-        B->ctas_per_sm = cand_ctas[i];
+    for (int i = 0; i < kCand; ++i) {
+        if (set_shape(B, cand_threads[i], cand_ctas[i], cand_cluster[i]) != EKCG_OK) continue;
         const int g = std::max(1, std::min<int>((int)((B->ntot + 255) / 256), B->num_sms * 8));
         k_gather_b<<<g, 256, 0, B->stream>>>(B->d_b, b, B->d_perm, B->ntot);
         EB_CUDA(cudaEventRecord(e0, B->stream));
@@ -710,17 +894,17 @@ int ekcg_batched_tune(ekcg_batch* B, const double* b, int s, double tol, int max
             best = ms;
             bt = cand_threads[i];
             bc = cand_ctas[i];
+            bk = cand_cluster[i];
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    B->threads = bt;
-    B->ctas_per_sm = bc;
-    if (B->graph) {
-        cudaGraphExecDestroy(B->graph);
-        B->graph = nullptr;
-    }
-    return EKCG_OK;
+    return set_shape(B, bt, bc, bk);
+}
+
+int ekcg_batched_set_shape(ekcg_batch* B, int threads, int ctas_per_sm, int cluster) {
+    if (!B) return EKCG_EINVAL;
+    return set_shape(B, threads, ctas_per_sm, cluster);
 }
 
 int ekcg_batched_solve(ekcg_batch* B, const double* b, int s, double tol, int maxit, double* x,
@@ -775,10 +959,13 @@ int ekcg_batched_solve(ekcg_batch* B, const double* b, int s, double tol, int ma
     return EKCG_OK;
 }
 
-int ekcg_batched_info(const ekcg_batch* B, int* threads, int* ctas_per_sm, double* last_ms) {
+int ekcg_batched_info(const ekcg_batch* B, int* threads, int* ctas_per_sm, int* cluster,
+                      int* groups, double* last_ms) {
     if (!B) return EKCG_EINVAL;
     if (threads) *threads = B->threads;
     if (ctas_per_sm) *ctas_per_sm = B->ctas_per_sm;
+    if (cluster) *cluster = B->cluster;
+    if (groups) *groups = B->groups;
     if (last_ms) *last_ms = B->last_ms;
     return EKCG_OK;
 }

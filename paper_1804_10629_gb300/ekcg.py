@@ -100,7 +100,10 @@ def _declare(L):
     L.ekcg_batched_solve.restype = c_int
     L.ekcg_batched_tune.argtypes = [c_void_p, c_void_p, c_int, c_double, c_int]
     L.ekcg_batched_tune.restype = c_int
-    L.ekcg_batched_info.argtypes = [c_void_p, POINTER(c_int), POINTER(c_int), POINTER(c_double)]
+    L.ekcg_batched_set_shape.argtypes = [c_void_p, c_int, c_int, c_int]
+    L.ekcg_batched_set_shape.restype = c_int
+    L.ekcg_batched_info.argtypes = [c_void_p, POINTER(c_int), POINTER(c_int), POINTER(c_int),
+                                    POINTER(c_int), POINTER(c_double)]
     L.ekcg_batched_info.restype = c_int
     L.ekcg_batched_destroy.argtypes = [c_void_p]
     L.ekcg_batched_destroy.restype = None
@@ -383,10 +386,17 @@ class BatchedSolver:
         if st != EKCG_OK:
             raise RuntimeError(lib().ekcg_batched_last_error().decode())
 
+    def set_shape(self, threads=512, ctas_per_sm=1, cluster=4):
+        st = lib().ekcg_batched_set_shape(self.h, int(threads), int(ctas_per_sm), int(cluster))
+        if st != EKCG_OK:
+            raise RuntimeError(f"ekcg_batched_set_shape: {strerror(st)}: "
+                               f"{lib().ekcg_batched_last_error().decode()}")
+
     def info(self):
-        th, cp, ms = c_int(), c_int(), c_double()
-        lib().ekcg_batched_info(self.h, byref(th), byref(cp), byref(ms))
-        return {"threads": th.value, "ctas_per_sm": cp.value, "last_ms": ms.value}
+        th, cp, cl, gr, ms = c_int(), c_int(), c_int(), c_int(), c_double()
+        lib().ekcg_batched_info(self.h, byref(th), byref(cp), byref(cl), byref(gr), byref(ms))
+        return {"threads": th.value, "ctas_per_sm": cp.value, "cluster": cl.value,
+                "groups": gr.value, "last_ms": ms.value}
 
     def close(self):
         if getattr(self, "h", None):

@@ -58,6 +58,73 @@ def test_batched_fp64_matches_oracle_per_system():
     B.close()
 
 
+_REFS = {}
+
+
+def oracle_refs(probs, key):
+    """Oracle solves of a batch, computed once per module."""
+    if key not in _REFS:
+        _REFS[key] = [o.solve(p.A, p.b, p.part, p.t, 2, tol=1e-8, maxit=2000) for p in probs]
+    return _REFS[key]
+
+
+@pytest.mark.parametrize("threads,ctas,cluster", [(512, 1, 1), (256, 2, 1), (512, 1, 2),
+                                                  (512, 1, 4), (512, 1, 8), (256, 2, 4)])
+def test_batched_launch_shapes_match_oracle(threads, ctas, cluster):
+    """Every launch shape -- one CTA per system, or a thread-block cluster of 2, 4 or 8 CTAs
+    splitting each system's rows and reducing through distributed shared memory -- against
+    the oracle, system by system (+-1 iteration, x to 1e-8); each shape reproduces its own
+    result bitwise on a second call."""
+    probs = small_batch(contrast=1.0)
+    refs = oracle_refs(probs, "contrast1")
+    B = ekcg.BatchedSolver(probs, 8, max_s=2)
+    B.set_shape(threads, ctas, cluster)
+    info = B.info()
+    assert (info["threads"], info["ctas_per_sm"], info["cluster"]) == (threads, ctas, cluster)
+    assert 1 <= info["groups"] <= len(probs)
+    x, it, st = B.solve(concat(probs), s=2, tol=1e-8, maxit=2000)
+    xs = split(x.cpu().numpy(), probs)
+    for k, (p, ref) in enumerate(zip(probs, refs)):
+        assert st[k] == ref.status == o.OK, (k, st[k], ref.status)
+        assert abs(int(it[k]) - ref.iters) <= 1, (k, it[k], ref.iters)
+        assert np.linalg.norm(xs[k] - ref.x) <= 1e-8 * np.linalg.norm(ref.x)
+    x2, it2, st2 = B.solve(concat(probs), s=2, tol=1e-8, maxit=2000)
+    assert np.array_equal(x.cpu().numpy(), x2.cpu().numpy()) and np.array_equal(it, it2)
+    B.close()
+
+
+def test_batched_cluster_wider_than_system():
+    """Systems with fewer rows than a cluster has CTAs (n = 6, 8, 9 with 8 CTAs per system):
+    the CTAs without rows contribute zero partial sums and still take every barrier."""
+    probs = []
+    for k, shape in enumerate([(3, 2), (4, 2), (3, 3), (10, 10)]):
+        A = wl.stencil_matrix(shape)
+        rng = np.random.default_rng(30 + k)
+        probs.append(wl.Problem(f"tiny-{k}", A, rng.uniform(-1, 1, A.n), 2,
+                                wl.partition_boxes(shape, 2), shape))
+    for cluster in (8, 1):
+        B = ekcg.BatchedSolver(probs, 2, max_s=2)
+        B.set_shape(512, 1, cluster)
+        x, it, st = B.solve(concat(probs), s=2, tol=1e-8, maxit=200)
+        xs = split(x.cpu().numpy(), probs)
+        for k, p in enumerate(probs):
+            ref = o.solve(p.A, p.b, p.part, 2, 2, tol=1e-8, maxit=200)
+            assert st[k] == ref.status, (cluster, k, st[k], ref.status)
+            assert abs(int(it[k]) - ref.iters) <= 1, (cluster, k, it[k], ref.iters)
+            assert np.linalg.norm(xs[k] - ref.x) <= 1e-8 * np.linalg.norm(ref.x)
+        B.close()
+
+
+def test_batched_set_shape_rejects_bad_values():
+    probs = small_batch(count=2, contrast=1.0)
+    B = ekcg.BatchedSolver(probs, 8, max_s=2)
+    for bad in [(128, 1, 1), (512, 3, 1), (512, 1, 3), (512, 1, 16)]:
+        with pytest.raises(RuntimeError):
+            B.set_shape(*bad)
+    assert B.info()["cluster"] == 4          # unchanged default
+    B.close()
+
+
 def test_batched_high_contrast_within_oracle_rounding_spread():
     """Coefficient jumps up to 1e4 (the batched configuration's recipe): s-step SRE-CG runs
     into loss of A-orthogonality and its iteration count moves by several iterations under
@@ -81,7 +148,8 @@ def test_batched_high_contrast_within_oracle_rounding_spread():
     B.close()
 
 
-def test_batched_mixed_reaches_tolerance_and_breakdown_is_per_system():
+@pytest.mark.parametrize("cluster", [1, 4])
+def test_batched_mixed_reaches_tolerance_and_breakdown_is_per_system(cluster):
     """Float32 inner solves converge only where kappa(A) * eps_float32 is well below 1;
     coefficient contrast <= 31 keeps kappa near 1e5 on these grids (the 1e4-contrast
     systems of the batched configuration reach kappa ~ 1e7-1e8, where float32 refinement
@@ -91,6 +159,7 @@ def test_batched_mixed_reaches_tolerance_and_breakdown_is_per_system():
     bad.b = bad.b.copy()
     bad.b[bad.part == 5] = 0.0            # T(r_0) has a zero column: breakdown
     B = ekcg.BatchedSolver(probs, 8, precision="fp32_ir", max_s=2)
+    B.set_shape(512, 1, cluster)
     x, it, st = B.solve(concat(probs), s=2, tol=1e-8, maxit=4000)
     xs = split(x.cpu().numpy(), probs)
     for k, p in enumerate(probs):
