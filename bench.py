@@ -29,6 +29,7 @@ import workloads as wl  # noqa: E402
 # FP64 ALU peak of one GB300: 152 SMs x 2 FP64 FMA per clock per SM x 2 flop x 2.07 GHz
 # (unit count inferred from a measured 1.20 TFLOP/s DFMA loop; the nominal figure is 1.25).
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 HBM_FALLBACK_GBS = 6800.0
 
 WORKLOADS = {
@@ -54,6 +55,8 @@ def parse():
     ap.add_argument("--variant", default="")
     ap.add_argument("--basis", default="sstep")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32_ir"])
+    ap.add_argument("--sweep", action="store_true",
+                    help="stability sweep over s in {1,2,4,8} and both precisions")
     ap.add_argument("--tol", type=float, default=1e-8)
     ap.add_argument("--maxit", type=int, default=20000)
     ap.add_argument("--cpu-sample-iters", type=int, default=2)
@@ -114,15 +117,21 @@ class Clocks:
 
 def measured_traffic(kernel_class):
     """DRAM bytes per algorithmic byte of a kernel class from the committed ncu record
-    (profiles/dominant_kernel_traffic.json), valid only while the kernel source it was
-    captured from is unchanged (sha256 of csrc/kernels.cuh)."""
+    (profiles/dominant_kernel_traffic.json).  Each class names the source files of its
+    kernels and the sha256 of their contents (in that order) at capture time; the ratio is
+    used only while those files are unchanged."""
     import hashlib
     try:
         rec = json.load(open(os.path.join(ROOT, "profiles", "dominant_kernel_traffic.json")))
-        src = open(os.path.join(ROOT, "paper_1804_10629_gb300", "csrc", "kernels.cuh"), "rb").read()
-        if rec.get("kernels_cuh_sha256") != hashlib.sha256(src).hexdigest():
+        c = rec.get("classes", {}).get(kernel_class)
+        if not c:
             return None
-        return rec.get("classes", {}).get(kernel_class)
+        h = hashlib.sha256()
+        for f in c["sources"]:
+            h.update(open(os.path.join(ROOT, f), "rb").read())
+        if c.get("sha256") != h.hexdigest():
+            return None
+        return c.get("ratio")
     except Exception:
         return None
 
@@ -147,6 +156,14 @@ def roofline_and_table(prof, args):
                     "traffic": traffic, "algorithmic_bytes_per_launch":
                         d["bytes"] / max(d["launches"], 1),
                     "launches": d["launches"], "avg_launch_ms": d["ms"] / max(d["launches"], 1)}
+        elif name == "gram_df":
+            # float-float Gram: bound by the FP32 pipe (10 FP32 operations per multiply-add)
+            ach = d["flops"] / sec / 1e12
+            roof = {"kernel": name, "bound": "alu", "achieved": ach,
+                    "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": ach / FP32_PEAK_TFLOPS,
+                    "peak_source": "derived FP32 FMA rate: 152 SMs x 128 FMA/clk x 2 x 2.07 GHz",
+                    "traffic": None, "launches": d["launches"],
+                    "avg_launch_ms": d["ms"] / max(d["launches"], 1)}
         else:
             peak = hbm or HBM_FALLBACK_GBS
             ach = d["bytes"] / sec / 1e9
@@ -188,12 +205,14 @@ class CudaTimer:
 
 def timed_solves(args, S, b, x, s, stream, dist, clocks, timer=None):
     """W warm-up solves, then K timed solves bracketed by barrier + synchronize, CUDA events
-    on the solve stream; per-kernel-class accounting summed over the timed solves; the step
-    time is the maximum over ranks."""
+    on the solve stream, with per-launch timing off; the step time is the maximum over
+    ranks.  Then one more solve with CUDA events around every launch (outside the timed
+    region) gives the per-kernel-class table, scaled to K solves."""
     import torch
     timer = timer or CudaTimer(stream)
     its = []
     st = 0
+    S.set_profile(False)
     for _ in range(args.warmup):
         _, it, _, st = S.solve(b, s=s, tol=args.tol, maxit=args.maxit, x=x)
         its.append(it)
@@ -209,12 +228,14 @@ def timed_solves(args, S, b, x, s, stream, dist, clocks, timer=None):
         _, it, hist, st = S.solve(b, s=s, tol=args.tol, maxit=args.maxit, x=x)
         its.append(it)
         launches += S.stats()[0]
-        for k, v in S.profile().items():
-            agg = prof.setdefault(k, {"ms": 0.0, "launches": 0, "flops": 0.0, "bytes": 0.0})
-            for f in agg:
-                agg[f] += v[f]
     timer.stop()
     timer.sync()
+    S.set_profile(True)
+    S.solve(b, s=s, tol=args.tol, maxit=args.maxit, x=x)
+    timer.sync()
+    for k, v in S.profile().items():
+        prof[k] = {f: v[f] * args.steps for f in ("ms", "launches", "flops", "bytes")}
+    S.set_profile(False)
     ck = clocks.stop() if clocks else None
     if dist:
         dist.barrier()
@@ -281,6 +302,51 @@ def run_batched(args, rank, world, dist):
             "gpu_launches": 3 * args.steps, "clocks": f["clocks"],
         }
         print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_sweep(args, rank):
+    """Stability sweep: s in {1, 2, 4, 8} x {float64, FP32_IR} on one workload (s-step SRE-CG,
+    Algorithm 4), one timed solve each after a short warm-up.  Per entry: s-step iterations,
+    status, time, true relative residual and the relative difference of x from the float64
+    s = 1 solution; per precision, the largest s that reached the tolerance."""
+    import torch
+    from paper_1804_10629_gb300 import ekcg
+    cfg = WORKLOADS[args.workload]
+    prob = cfg["make"](args.grid)
+    b = torch.as_tensor(prob.b, dtype=torch.float64, device="cuda")
+    Asp = prob.A.to_scipy()
+    nb = float(np.linalg.norm(prob.b))
+    rows, ref = [], None
+    for prec in ("fp64", "fp32_ir"):
+        for s in (1, 2, 4, 8):
+            S = ekcg.Solver(prob.A, prob.t, prob.part, variant="sre", precision=prec, max_s=s)
+            x = torch.empty_like(b)
+            S.solve(b, s=s, tol=args.tol, maxit=20, x=x)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            x, its, hist, st = S.solve(b, s=s, tol=args.tol, maxit=args.maxit, x=x)
+            e1.record()
+            torch.cuda.synchronize()
+            xs = x.cpu().numpy()
+            if ref is None:
+                ref = xs.copy()
+            rows.append({"precision": prec, "s": s, "iters": int(its), "status": int(st),
+                         "seconds": e0.elapsed_time(e1) / 1e3,
+                         "true_relres": float(np.linalg.norm(prob.b - Asp @ xs) / nb),
+                         "x_rel_diff_vs_fp64_s1": float(np.linalg.norm(xs - ref) /
+                                                        np.linalg.norm(ref))})
+            S.close()
+    largest = {}
+    for prec in ("fp64", "fp32_ir"):
+        ok = [r["s"] for r in rows if r["precision"] == prec and r["status"] == 0
+              and r["true_relres"] <= args.tol * 1.01]
+        largest[prec] = max(ok) if ok else None
+    if rank == 0:
+        print(json.dumps({"sweep": prob.name, "n": prob.A.n, "t": prob.t, "tol": args.tol,
+                          "rows": rows, "largest_stable_s": largest}), flush=True)
     return 0
 
 
@@ -425,6 +491,8 @@ def main():
         from paper_1804_10629_gb300 import build
         build.build()
 
+    if args.sweep:
+        return run_sweep(args, rank)
     if args.workload == "batched":
         return run_batched(args, rank, world, dist)
     if args.workload == "diff2d":
@@ -464,11 +532,15 @@ def main():
         rr_m = float(np.linalg.norm(prob.b - prob.A.to_scipy() @ xmh) / np.linalg.norm(prob.b))
         pk = peaks().get("hbm_gbs") or HBM_FALLBACK_GBS
         hbm = {}
-        for k in ("spmm", "gram", "block_update"):
+        for k in ("spmm", "gram", "block_update", "gram_df"):
             d = rm["prof"].get(k)
             if d and d["ms"] > 0:
                 gbs = d["bytes"] / (d["ms"] / 1e3) / 1e9
                 hbm[k] = {"gbs": gbs, "frac": gbs / pk, "ms_per_step": d["ms"] / args.steps}
+                if k == "gram_df":
+                    tf = d["flops"] / (d["ms"] / 1e3) / 1e12
+                    hbm[k]["fp32_tflops"] = tf
+                    hbm[k]["fp32_frac"] = tf / FP32_PEAK_TFLOPS
         mixed = {"value": rm["ms"] / 1e3, "unit": "s", "iters": rm["iters"], "status": rm["status"],
                  "true_relres": rr_m, "speedup_vs_fp64": ms_step / rm["ms"],
                  "hbm": hbm, "hbm_peak_gbs": pk,
@@ -511,7 +583,7 @@ def main():
                        "true_relres": relres, "status": st,
                        "l2": "working set larger than L2 (matrix + n x t blocks)",
                        "setup_s": setup_s, "parallelism": "replicas",
-                       "profiling": "CUDA events around every launch on the solve stream"},
+                       "profiling": "timed solves without per-launch events; kernel table from one more solve with CUDA events around every launch"},
             "roofline": roof, "kernels": kernel_table, "gpu_launches": launches,
             "mixed": mixed,
             "e2e": e2e, "cpu_baseline": cpu, "clocks": ck,

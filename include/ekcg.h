@@ -136,6 +136,10 @@ int ekcg_get_perm(const ekcg_ctx* ctx, int64_t* perm);
 /* Kernel launches and sparse products of the last solve.                                 */
 int ekcg_last_stats(const ekcg_ctx* ctx, int64_t* kernel_launches, int64_t* spmm_calls);
 
+/* Turn the per-launch CUDA-event timing of later solves on (on != 0) or off, whatever
+ * opts.profile was at setup.  Errors: EKCG_EINVAL (NULL ctx).                            */
+int ekcg_set_profile(ekcg_ctx* ctx, int on);
+
 /* Per-kernel-class accounting of the last solve: for class i < *count, names[i] (static
  * strings), launches[i], flops[i] and bytes[i] (algorithmic: the arithmetic the method needs
  * and the compulsory DRAM traffic of each launch, summed), and ms[i], the total device time

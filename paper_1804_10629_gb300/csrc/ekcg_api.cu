@@ -11,10 +11,12 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/ekcg.h"
 #include "kernels.cuh"
+#include "bulk.cuh"
 
 using namespace ekcg;
 
@@ -43,11 +45,13 @@ void set_error(const char* where, const char* what) {
 
 enum KClass {
     KC_SPMM = 0, KC_GRAM, KC_REDUCE, KC_UPDATE, KC_CHOL, KC_XR, KC_RESID, KC_SPLIT, KC_PERM,
-    KC_COPY, KC_NORM, KC_MISC, KC_COUNT
+    KC_COPY, KC_NORM, KC_MISC, KC_GRAM_DF, KC_COUNT
 };
+// gram_df: the float-float upper-triangle Gram of the float32 path (FP32-pipe bound; its
+// operation count is 10 FP32 operations per multiply-add)
 const char* kClassNames[KC_COUNT] = {"spmm", "gram", "gram_reduce", "block_update", "chol_inv",
                                      "xr_update", "residual", "split_T", "permute", "copy",
-                                     "norm", "misc"};
+                                     "norm", "misc", "gram_df"};
 
 }  // namespace
 
@@ -262,8 +266,81 @@ int launch_gram_warp(ekcg_ctx* c, MB<const float> X, MB<const float> Y, Acc* par
     return EKCG_OK;
 }
 
+// Upper triangle (i <= j) of the Gram of two single n x M blocks, M = 16 or 32 (bulk.cuh;
+// float-float accumulation for float data), then the CTA-order reduction; the entries below
+// the computed lane blocks are zero.
+template <typename T, int M>
+int launch_gram_upper(ekcg_ctx* c, const T* X, const T* Y, double* C) {
+    using U = bulk::UpperShape<T, M>;
+    static int per_sm = -1;
+    if (per_sm < 0) {
+        EK_CUDA(cudaFuncSetAttribute(bulk::k_gram_upper<T, M>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)U::kSmem));
+        int b = 0;
+        EK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, bulk::k_gram_upper<T, M>,
+                                                              bulk::kUThreads, U::kSmem));
+        per_sm = std::max(1, b);
+    }
+    const int64_t ntile = (c->n + U::kTR - 1) / U::kTR;
+    const int64_t gcap = std::min<int64_t>((int64_t)c->num_sms * per_sm,
+                                           c->cap_partials / (kGramTile * kGramTile));
+    const int g = (int)std::max<int64_t>(1, std::min<int64_t>(ntile, gcap));
+    {
+        // float: 10 FP32 operations per float-float multiply-add (class gram_df); float64:
+        // 2 flops per multiply-add (class gram); M (M + 1) / 2 multiply-adds per row
+        const bool df = sizeof(T) == sizeof(float);
+        Launch L(c, df ? KC_GRAM_DF : KC_GRAM, (df ? 5.0 : 1.0) * (double)c->n * M * (M + 1),
+                 2.0 * (double)c->n * M * sizeof(T));
+        bulk::k_gram_upper<T, M><<<g, bulk::kUThreads, U::kSmem, c->stream>>>(
+            X, Y, c->n, c->partials, c->flag);
+    }
+    EK_TRY(check_launch("k_gram_upper"));
+    Launch L(c, KC_REDUCE, (double)g * M * M, (double)g * M * M * sizeof(double));
+    k_gram_reduce<double, double><<<reduce_grid(M * M, c->num_sms), kThreads, 0, c->stream>>>(
+        c->partials, g, 1, M, M, M, M, C, M, 0);
+    return check_launch("k_gram_reduce");
+}
+
+// float64 CGS coefficient Gram through the bulk-staged kernel (bulk.cuh).
+template <int P, int Q, int MP, int MQ>
+int launch_gram_bulk_f64(ekcg_ctx* c, MB<const double> X, MB<const double> Y, double* partials,
+                         int* g) {
+    using S = bulk::GramBulkShape<P, Q>;
+    static int per_sm = -1;
+    if (per_sm < 0) {
+        EK_CUDA(cudaFuncSetAttribute(bulk::k_gram_bulk_f64<P, Q, MP, MQ>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::kSmem));
+        int b = 0;
+        EK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &b, bulk::k_gram_bulk_f64<P, Q, MP, MQ>, bulk::kThreads, S::kSmem));
+        per_sm = std::max(1, b);
+    }
+    const int64_t ntile = (c->n + bulk::kGR - 1) / bulk::kGR;
+    const int64_t gcap = std::min<int64_t>((int64_t)c->num_sms * per_sm,
+                                           c->cap_partials / (kGramTile * kGramTile));
+    *g = (int)std::max<int64_t>(1, std::min<int64_t>(ntile, gcap));
+    Launch L(c, KC_GRAM, 2.0 * (double)c->n * P * Q, (double)c->n * (P + Q) * sizeof(double));
+    bulk::k_gram_bulk_f64<P, Q, MP, MQ><<<*g, bulk::kThreads, S::kSmem, c->stream>>>(
+        X, Y, c->n, partials, c->flag);
+    return EKCG_OK;
+}
+
 template <typename T, typename Acc>
 bool gram_fast_path(ekcg_ctx* c, MB<const T> X, MB<const T> Y, Acc* partials, int* g, int* rc) {
+    return false;
+}
+template <>
+bool gram_fast_path<double, double>(ekcg_ctx* c, MB<const double> X, MB<const double> Y,
+                                    double* partials, int* g, int* rc) {
+    const int P = X.cols(), Q = Y.cols();
+    auto al = [](const MB<const double>& m) {
+        return (m.stride % 2) == 0 && ((uintptr_t)m.base % 16) == 0;
+    };
+    if (Y.count != 1 || X.w != Q || Y.w != Q || !al(X) || !al(Y)) return false;
+    if (P == 64 && Q == 32) { *rc = launch_gram_bulk_f64<64, 32, 2, 4>(c, X, Y, partials, g); return true; }
+    if (P == 32 && Q == 32) { *rc = launch_gram_bulk_f64<32, 32, 2, 2>(c, X, Y, partials, g); return true; }
+    if (P == 32 && Q == 16) { *rc = launch_gram_bulk_f64<32, 16, 2, 1>(c, X, Y, partials, g); return true; }
+    if (P == 16 && Q == 16) { *rc = launch_gram_bulk_f64<16, 16, 1, 1>(c, X, Y, partials, g); return true; }
     return false;
 }
 template <typename Acc>
@@ -305,11 +382,10 @@ int run_gram_chunk(ekcg_ctx* c, MB<const T> X, MB<const T> Y, Out* C, int ldc, i
         int gfast = 0, rc = EKCG_OK;
         if (gram_fast_path<T, Acc>(c, X, Y, partials, &gfast, &rc)) {
             if (rc != EKCG_OK) return rc;
-            EK_TRY(check_launch("k_gram_warp_f32"));
+            EK_TRY(check_launch("k_gram fast path"));
             Launch L(c, KC_REDUCE, (double)gfast * P * Q, (double)gfast * P * Q * sizeof(Acc));
-            int gr = std::max(1, std::min((P * Q + kThreads - 1) / kThreads, c->num_sms * 4));
-            k_gram_reduce<Acc, Out><<<gr, kThreads, 0, c->stream>>>(partials, gfast, 1, P, Q, P,
-                                                                    Q, C, ldc, c_row0);
+            k_gram_reduce<Acc, Out><<<reduce_grid(P * Q, c->num_sms), kThreads, 0, c->stream>>>(
+                partials, gfast, 1, P, Q, P, Q, C, ldc, c_row0);
             return check_launch("k_gram_reduce");
         }
     }
@@ -339,6 +415,14 @@ int run_gram_chunk(ekcg_ctx* c, MB<const T> X, MB<const T> Y, Out* C, int ldc, i
     } else if (Q > 1) {
         TQ = 4;
         EK_TRY((gram_shape<T, Acc, 64, 4, 1, 1>(c, X, Y, partials, &ntq)));
+    } else if (P <= kThreads && Y.count == 1 && Y.w == 1) {
+        // one right-hand vector (alpha = V^T r): the row-coalesced vector kernel
+        // (one partial column per CTA: tile 0, entry p)
+        TQ = 1;
+        TP = P;
+        Launch L(c, KC_GRAM, 2.0 * (double)c->n * P, (double)c->n * (P + 1) * sizeof(T));
+        k_gram_vec<T, Acc><<<c->grid_rows, kThreads, 0, c->stream>>>(X, Y.blk(0), c->n,
+                                                                     partials);
     } else {
         TQ = 1;
         TP = 256;
@@ -348,10 +432,8 @@ int run_gram_chunk(ekcg_ctx* c, MB<const T> X, MB<const T> Y, Out* C, int ldc, i
     const int g = c->grid_rows;
     {
         Launch L(c, KC_REDUCE, (double)g * P * Q, (double)g * P * Q * sizeof(Acc));
-        int tot = P * Q;
-        int gr = std::max(1, std::min((tot + kThreads - 1) / kThreads, c->num_sms * 4));
-        k_gram_reduce<Acc, Out><<<gr, kThreads, 0, c->stream>>>(partials, g, ntq, TP, TQ, P, Q,
-                                                                C, ldc, c_row0);
+        k_gram_reduce<Acc, Out><<<reduce_grid(P * Q, c->num_sms), kThreads, 0, c->stream>>>(
+            partials, g, ntq, TP, TQ, P, Q, C, ldc, c_row0);
     }
     return check_launch("k_gram_reduce");
 }
@@ -370,6 +452,20 @@ int run_gram(ekcg_ctx* c, MB<const T> X, MB<const T> Y, Out* C, Acc* partials) {
     return EKCG_OK;
 }
 
+// Gram whose consumer reads only the upper triangle (the Cholesky of A-CholQR and
+// Pre-CholQR): float32 single blocks of width 16 or 32 take the upper-triangle float-float
+// kernel; everything else the full Gram.
+template <typename T>
+int run_gram_upper(ekcg_ctx* c, MB<const T> X, MB<const T> Y, double* C) {
+    const int M = X.cols();
+    const bool fits = X.count == 1 && Y.count == 1 && X.w == Y.w && (M == 16 || M == 32) &&
+                      ((uintptr_t)X.blk(0) % 16) == 0 && ((uintptr_t)Y.blk(0) % 16) == 0;
+    if (fits)
+        return M == 32 ? launch_gram_upper<T, 32>(c, X.blk(0), Y.blk(0), C)
+                       : launch_gram_upper<T, 16>(c, X.blk(0), Y.blk(0), C);
+    return run_gram<T, double, double>(c, X, Y, C, c->partials);
+}
+
 // float32, 16-byte-aligned shapes: the register-row kernel (see k_update_f32).
 template <int P>
 int launch_update_f32(ekcg_ctx* c, MB<const float> X, const float* C, int ldc, int c_row0,
@@ -378,6 +474,28 @@ int launch_update_f32(ekcg_ctx* c, MB<const float> X, const float* C, int ldc, i
     const int g = (int)std::min<int64_t>((work + 255) / 256, (int64_t)c->num_sms * 8);
     k_update_f32<P><<<g, 256, 0, c->stream>>>(X, C, ldc, c_row0, Y, OUT, c->n, beta_on, alpha,
                                               upper);
+    return EKCG_OK;
+}
+
+// TMA-staged float32 update (bulk.cuh): grid = resident CTAs (by shared memory), at most one
+// per row tile.
+template <int P, int Q>
+int launch_update_bulk(ekcg_ctx* c, MB<const float> X, const float* C, int ldc, int c_row0,
+                       MB<const float> Y, MB<float> OUT, int beta_on, float alpha) {
+    using S = bulk::Shape<P, Q>;
+    static int per_sm = -1;   // resident CTAs per SM for this shape (same on every GB300)
+    if (per_sm < 0) {
+        EK_CUDA(cudaFuncSetAttribute(bulk::k_update_bulk_f32<P, Q>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::kSmem));
+        int b = 0;
+        EK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, bulk::k_update_bulk_f32<P, Q>,
+                                                              bulk::kThreads, S::kSmem));
+        per_sm = std::max(1, b);
+    }
+    const int64_t ntile = (c->n + S::kTR - 1) / S::kTR;
+    const int g = (int)std::min<int64_t>(ntile, (int64_t)c->num_sms * per_sm);
+    bulk::k_update_bulk_f32<P, Q><<<g, bulk::kThreads, S::kSmem, c->stream>>>(
+        X, C, ldc, c_row0, Y, OUT, c->n, beta_on, alpha, c->flag);
     return EKCG_OK;
 }
 
@@ -396,11 +514,25 @@ bool update_fast_path<float, float>(ekcg_ctx* c, MB<const float> X, const float*
                ((uintptr_t)m.base % 16) == 0;
     };
     if (Q % 4 || Q > 32 || !al(X) || !al(as_const(OUT)) || (beta_on && !al(Y))) return false;
-    // in place on X (W <- W R^{-1}): the warp-synchronous triangular kernel
     bool inplace = false;
     for (int a = 0; a < X.count; ++a)
         for (int b = 0; b < OUT.count; ++b)
             if (X.blk(a) == (const float*)OUT.blk(b)) inplace = true;
+    // TMA-staged kernel for block widths 16 and 32: the CGS update (X = one or two window
+    // blocks) and the in-place product with R^{-1} (upper triangular, zero below)
+    const bool shapes_ok = X.w == Q && OUT.count == 1 && OUT.w == Q &&
+                           (!beta_on || (Y.count == 1 && Y.w == Q)) &&
+                           (!inplace || (X.count == 1 && !beta_on && alpha == 1.f));
+    if (shapes_ok && (Q == 16 || Q == 32) && (P == Q || P == 2 * Q)) {
+        if (Q == 32)
+            *rc = P == 64 ? launch_update_bulk<64, 32>(c, X, C, ldc, c_row0, Y, OUT, beta_on, alpha)
+                          : launch_update_bulk<32, 32>(c, X, C, ldc, c_row0, Y, OUT, beta_on, alpha);
+        else
+            *rc = P == 32 ? launch_update_bulk<32, 16>(c, X, C, ldc, c_row0, Y, OUT, beta_on, alpha)
+                          : launch_update_bulk<16, 16>(c, X, C, ldc, c_row0, Y, OUT, beta_on, alpha);
+        return true;
+    }
+    // in place on X (W <- W R^{-1}): the warp-synchronous triangular kernel
     if (inplace) {
         if (!upper || beta_on || P != Q || alpha != 1.f || X.count != OUT.count) return false;
         const int64_t work = c->n * (Q / 4);
@@ -599,16 +731,14 @@ struct Engine {
         if (c->opts.orth == EKCG_PRECHOLQR) {
             // Euclidean CholQR2: W = Z S, applied to W and A W alike.
             for (int rep = 0; rep < 2; ++rep) {
-                EK_TRY((run_gram<T, double, double>(c, as_const(Wm(j, cnt)),
-                                                    as_const(Wm(j, cnt)), c->G, c->partials)));
+                EK_TRY(run_gram_upper<T>(c, as_const(Wm(j, cnt)), as_const(Wm(j, cnt)), c->G));
                 EK_TRY(run_chol(c, m));
                 const T* Ri = rinv_for<T>(c, m);
                 EK_TRY((run_rmul<T, T>(c, Wm(j, cnt), Ri)));
                 EK_TRY((run_rmul<T, T>(c, Zm(j, cnt), Ri)));
             }
         }
-        EK_TRY((run_gram<T, double, double>(c, as_const(Wm(j, cnt)), as_const(Zm(j, cnt)), c->G,
-                                            c->partials)));
+        EK_TRY(run_gram_upper<T>(c, as_const(Wm(j, cnt)), as_const(Zm(j, cnt)), c->G));
         EK_TRY(run_chol(c, m));
         const T* Ri = rinv_for<T>(c, m);
         EK_TRY((run_rmul<T, T>(c, Wm(j, cnt), Ri)));
@@ -717,8 +847,20 @@ struct Engine {
         {
             const double nn = (double)n, stc = (double)s * t;
             Launch L(c, KC_XR, 4.0 * nn * stc + 2.0 * nn, nn * (2.0 * stc + 4.0) * sizeof(T));
-            k_xr_update<T><<<c->grid_red, kThreads, 0, c->stream>>>(
-                x, r, as_const(Wm(v0, s)), as_const(Zm(v0, s)), c->alpha, n, c->red, c->flag);
+            const MB<const T> V = as_const(Wm(v0, s)), AV = as_const(Zm(v0, s));
+            const int g4 = t / 4;
+            const bool f32_rows = std::is_same<T, float>::value && t % 4 == 0 && g4 <= 32 &&
+                                  (g4 & (g4 - 1)) == 0 && s * t <= kMaxAlpha &&
+                                  ((uintptr_t)V.base % 16) == 0 && V.stride % 4 == 0 &&
+                                  ((uintptr_t)AV.base % 16) == 0 && AV.stride % 4 == 0;
+            if constexpr (std::is_same<T, float>::value) {
+                if (f32_rows)
+                    k_xr_update_f32<<<c->grid_red, kThreads, 0, c->stream>>>(x, r, V, AV, c->alpha,
+                                                                             n, c->red, c->flag);
+            }
+            if (!f32_rows)
+                k_xr_update<T><<<c->grid_red, kThreads, 0, c->stream>>>(x, r, V, AV, c->alpha, n,
+                                                                        c->red, c->flag);
         }
         EK_TRY(check_launch("k_xr_update"));
         {
@@ -779,6 +921,10 @@ int sstep_loop(ekcg_ctx* c, int s, double tol_abs, int maxit, T* x, T* r, double
         if (rc != EKCG_OK) return rc;
         EK_TRY(E.update(v0));
         EK_TRY(sync_read(c, &rho, &flag));
+        if (flag & 4) {
+            set_error("ekcg_solve", "a staged bulk copy did not complete within its wait limit");
+            return EKCG_ETIMEOUT;
+        }
         if (flag & 1) {
             status = EKCG_EBREAKDOWN;
             break;
@@ -1288,6 +1434,12 @@ int ekcg_last_stats(const ekcg_ctx* c, int64_t* kl, int64_t* sp) {
     if (!c) return EKCG_EINVAL;
     if (kl) *kl = c->launches;
     if (sp) *sp = c->spmm_calls;
+    return EKCG_OK;
+}
+
+int ekcg_set_profile(ekcg_ctx* c, int on) {
+    if (!c) return EKCG_EINVAL;
+    c->opts.profile = on ? 1 : 0;
     return EKCG_OK;
 }
 

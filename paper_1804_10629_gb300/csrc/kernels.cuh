@@ -426,20 +426,74 @@ k_gram_warp_f32(MB<const float> X, MB<const float> Y, int64_t n, Acc* __restrict
     }
 }
 
-// C[(c_row0 + p)*ldc + q] = sum over CTAs of the partials, p < P, q < Q.
+// Block times one vector, c = X^T r (the s-step coefficients alpha = V^T r): P <= 256
+// columns of X, one right-hand column.  Thread (phase ph, column p) walks rows
+// ph, ph + phases, ... of the CTA's row stripe: the P threads of a phase read one row of every
+// block of X contiguously and r[row] by broadcast; eight rows are loaded before they are
+// added.  The phases of a CTA are summed in phase order into its partial (partials[cta*4096
+// + p]); k_gram_reduce then sums the CTAs in order.
+template <typename T, typename Acc>
+__global__ void __launch_bounds__(kThreads)
+k_gram_vec(MB<const T> X, const T* __restrict__ r, int64_t n, Acc* __restrict__ partials) {
+    __shared__ Acc red[kThreads];
+    const int P = X.cols();
+    const int phases = kThreads / P;
+    const int tid = threadIdx.x;
+    const bool active = tid < phases * P;
+    const int p = active ? tid % P : 0, ph = active ? tid / P : 0;
+    const int b = p / X.w, cc = p - b * X.w;
+    const T* xb = X.blk(b);
+    const int64_t stride = (int64_t)gridDim.x * phases;
+    Acc acc = Acc(0);
+    if (active) {
+        int64_t row = (int64_t)blockIdx.x * phases + ph;
+        for (; row + 7 * stride < n; row += 8 * stride) {
+            T xv[8], rv[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                xv[u] = xb[(row + u * stride) * X.w + cc];
+                rv[u] = r[row + u * stride];
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) acc += (Acc)xv[u] * (Acc)rv[u];
+        }
+        for (; row < n; row += stride) acc += (Acc)xb[row * X.w + cc] * (Acc)r[row];
+    }
+    red[tid] = acc;
+    __syncthreads();
+    for (int q = tid; q < P; q += kThreads) {
+        Acc s = Acc(0);
+        for (int h = 0; h < phases; ++h) s += red[h * P + q];
+        partials[(int64_t)blockIdx.x * (kGramTile * kGramTile) + q] = s;
+    }
+}
+
+// C[(c_row0 + p)*ldc + q] = sum over the g CTAs of the partials, p < P, q < Q.  One warp per
+// output: lane l adds the partials of CTAs l, l + 32, ... in CTA order, and the 32 lane sums
+// are combined by a fixed shuffle tree (the same order on every call).
 template <typename Acc, typename Out>
 __global__ void k_gram_reduce(const Acc* __restrict__ partials, int g, int ntq, int TP, int TQ,
                               int P, int Q, Out* __restrict__ C, int ldc, int c_row0) {
     const int total = P * Q;
-    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
+    const int lane = threadIdx.x & 31;
+    const int nwarps = (int)((gridDim.x * blockDim.x) >> 5);
+    for (int e = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); e < total; e += nwarps) {
         const int p = e / Q, q = e - p * Q;
         const int tile = (p / TP) * ntq + q / TQ;
         const int loc = (p % TP) * TQ + (q % TQ);
         const Acc* src = partials + (int64_t)tile * g * (kGramTile * kGramTile) + loc;
         Acc s = Acc(0);
-        for (int c = 0; c < g; ++c) s += src[(int64_t)c * (kGramTile * kGramTile)];
-        C[(int64_t)(c_row0 + p) * ldc + q] = (Out)s;
+        for (int c = lane; c < g; c += 32) s += src[(int64_t)c * (kGramTile * kGramTile)];
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) C[(int64_t)(c_row0 + p) * ldc + q] = (Out)s;
     }
+}
+
+// CTAs for k_gram_reduce: one warp per output, at most 4 CTAs per SM.
+inline int reduce_grid(int outputs, int num_sms) {
+    const int warps_per_cta = kThreads / 32;
+    const int need = (outputs + warps_per_cta - 1) / warps_per_cta;
+    return need < 1 ? 1 : (need < num_sms * 4 ? need : num_sms * 4);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -709,6 +763,65 @@ k_xr_update(T* __restrict__ x, T* __restrict__ r, MB<const T> V, MB<const T> Z,
             x[i] = xi;
             r[i] = ri;
             local += (double)ri * (double)ri;
+        }
+    }
+    const double s = block_sum(local, red);
+    if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
+// float32 x/r update of the inner solve: x += V alpha, r -= (A V) alpha in float arithmetic
+// (alpha rounded to float).  The w/4 consecutive threads of a row (w/4 a power of two <= 32,
+// so they share a warp) each take one float4 of every block and combine their partial sums
+// with shuffles in a fixed order; the row's first thread writes x and r and adds r^2
+// (float64) to the CTA partial of ||r||^2.  The loop runs over whole warps so that every
+// lane reaches the shuffles.  Skipped after a breakdown, like k_xr_update.
+constexpr int kMaxAlpha = 1024;
+__global__ void __launch_bounds__(kThreads)
+k_xr_update_f32(float* __restrict__ x, float* __restrict__ r, MB<const float> V,
+                MB<const float> Z, const double* __restrict__ alpha, int64_t n,
+                double* __restrict__ partials, const int* __restrict__ flag) {
+    __shared__ float al[kMaxAlpha];
+    __shared__ double red[32];
+    const int w = V.w, g4 = w / 4, m = V.count * w;
+    for (int i = threadIdx.x; i < m; i += blockDim.x) al[i] = (float)alpha[i];
+    __syncthreads();
+    const bool skip = (*flag) != 0;
+    double local = 0.0;
+    if (!skip) {
+        const int64_t total = n * g4;
+        const int64_t span = (total + 31) / 32 * 32;
+        const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+        for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < span; e += stride) {
+            const bool live = e < total;
+            const int64_t i = live ? e / g4 : 0;
+            const int q = live ? (int)(e - i * g4) : 0;
+            float sx = 0.f, sr = 0.f;
+            if (live) {
+                for (int b = 0; b < V.count; ++b) {
+                    const float4 v = *reinterpret_cast<const float4*>(V.blk(b) + i * w + 4 * q);
+                    const float4 z = *reinterpret_cast<const float4*>(Z.blk(b) + i * w + 4 * q);
+                    const float* a = al + b * w + 4 * q;
+                    sx += v.x * a[0];
+                    sx += v.y * a[1];
+                    sx += v.z * a[2];
+                    sx += v.w * a[3];
+                    sr += z.x * a[0];
+                    sr += z.y * a[1];
+                    sr += z.z * a[2];
+                    sr += z.w * a[3];
+                }
+            }
+            for (int o = g4 / 2; o > 0; o >>= 1) {
+                sx += __shfl_xor_sync(0xffffffffu, sx, o);
+                sr += __shfl_xor_sync(0xffffffffu, sr, o);
+            }
+            if (live && q == 0) {
+                const float xi = x[i] + sx;
+                const float ri = r[i] - sr;
+                x[i] = xi;
+                r[i] = ri;
+                local += (double)ri * (double)ri;
+            }
         }
     }
     const double s = block_sum(local, red);

@@ -67,6 +67,8 @@ def _declare(L):
     L.ekcg_get_perm.restype = c_int
     L.ekcg_last_stats.argtypes = [c_void_p, POINTER(c_int64), POINTER(c_int64)]
     L.ekcg_last_stats.restype = c_int
+    L.ekcg_set_profile.argtypes = [c_void_p, c_int]
+    L.ekcg_set_profile.restype = c_int
     L.ekcg_profile.argtypes = [c_void_p, c_int, POINTER(c_char_p), POINTER(c_double),
                                POINTER(c_int64), POINTER(c_double), POINTER(c_double),
                                POINTER(c_int)]
@@ -337,6 +339,10 @@ class Solver:
 
     def profile(self):
         return ekcg_profile(self.ctx)
+
+    def set_profile(self, on):
+        """Per-launch CUDA-event timing of later solves on or off."""
+        lib().ekcg_set_profile(self.ctx, int(bool(on)))
 
 
 class BatchedSolver:

@@ -52,6 +52,9 @@ class _FakeSolver:
     def profile(self):
         return {"gram": {"ms": 1.0, "launches": 2, "flops": 10.0, "bytes": 20.0}}
 
+    def set_profile(self, on):
+        self.profiling = bool(on)
+
 
 def _worker(rank, world, port, out):
     sys.path.insert(0, ROOT)

@@ -277,6 +277,21 @@ def test_fp32_ir_reaches_fp64_accuracy(variant):
     S.close()
 
 
+@pytest.mark.parametrize("orth", ["acholqr", "precholqr"])
+def test_fp32_ir_upper_gram_orthonormalisations(orth):
+    """The float32 path forms the A-CholQR Gram W^T (A W) and the Pre-CholQR Gram W^T W
+    upper-triangle only (float-float accumulation) for block widths 16 and 32: both
+    orthonormalisations reach the float64 tolerance on a t = 16 Sky3D-like case."""
+    A = wl.stencil_matrix((16, 16, 16), kappa=wl.kappa_skyscraper3d(16))
+    part = wl.partition_boxes((16, 16, 16), 16)
+    b = wl.rhs_uniform(A.n, 3)
+    S = ekcg.Solver(A, 16, part, orth=orth, precision="fp32_ir", max_s=2)
+    x, it, hist, st = S.solve(dev(b), s=2, tol=1e-8, maxit=5000)
+    assert st == 0
+    assert relres(A, b, x.cpu().numpy()) <= 1e-8 * 1.01
+    S.close()
+
+
 @pytest.mark.parametrize("s", [1, 2])
 def test_fp32_ir_ani3d_t32(s):
     """t = 32 exercises the float32 register-row update (P = 64 window, P = 32 triangular)
@@ -329,16 +344,22 @@ def test_sky3d_full_size_against_oracle_record():
     """Sky3D-like 96^3 (coefficient 1 / 1e3 on 8^3 blocks), t = 16, s = 4, float64: the
     iteration count and the first 21 residual norms against the oracle's whole-solve
     record (tests/golden/oracle_counts.json, written by the oracle only), and the true
-    relative residual."""
+    relative residual.  s-step SRE-CG with s = 4 on this 1e3-contrast problem loses
+    A-orthogonality as the iteration proceeds, so its iteration count moves under
+    rounding-level changes; the record also holds the oracle's own counts with b perturbed
+    by 1e-15 (relative), and the GPU count must lie within that range widened by one."""
     import json
     gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden",
                                        "oracle_counts.json")))
-    g = gold["sky3d/t16/s4/sre/sstep/fp64"]
+    key = "sky3d/t16/s4/sre/sstep/fp64"
+    g = gold[key]
+    counts = [g["iters"]] + [v["iters"] for k, v in gold.items()
+                             if k.startswith(key + "/perturbed/")]
     p = wl.sky3d(96, 16, seed=2)
     S = ekcg.Solver(p.A, 16, p.part, max_s=4)
     x, it, hist, st = S.solve(dev(p.b), s=4, tol=1e-8, maxit=5000)
     assert st == 0
-    assert abs(it - g["iters"]) <= 1, (it, g["iters"])
+    assert min(counts) - 1 <= it <= max(counts) + 1, (it, counts)
     np.testing.assert_allclose(hist[:21], g["hist"][:21], rtol=1e-6)
     assert relres(p.A, p.b, x.cpu().numpy()) <= 1e-8 * 1.01
     S.close()
