@@ -108,7 +108,8 @@ def test_spmm_matches_scipy(w):
     S.close()
 
 
-@pytest.mark.parametrize("p,q", [(64, 32), (32, 32), (16, 16), (48, 8), (64, 1), (256, 16)])
+@pytest.mark.parametrize("p,q", [(64, 32), (32, 32), (16, 16), (48, 8), (64, 1), (48, 1), (256, 1),
+                                 (256, 16)])
 def test_gram_entry_matches_numpy(p, q):
     """C = X^T Y over n = 1665 rows (ragged against the 32-row stages), tolerance
     n * eps * |X|^T |Y| (the float64 dot-product error bound)."""
