@@ -136,6 +136,14 @@ int ekcg_get_perm(const ekcg_ctx* ctx, int64_t* perm);
 /* Kernel launches and sparse products of the last solve.                                 */
 int ekcg_last_stats(const ekcg_ctx* ctx, int64_t* kernel_launches, int64_t* spmm_calls);
 
+/* Diagnostic, no counterpart in the paper: runs the bounded mbarrier wait of the
+ * bulk-copy-staged kernels on a stage that never completes (16 bytes expected, no copy
+ * issued), with a limit of limit_cycles SM cycles (1 .. 2^32), on `stream` (NULL = default
+ * stream).  Returns EKCG_ETIMEOUT when the wait ran out and reported it, as the staged
+ * kernels do; EKCG_EINVAL for a limit out of range; EKCG_ENOMEM / EKCG_ECUDA.  The device
+ * stays usable afterwards.  Allocates and frees one int.                                 */
+int ekcg_wait_selftest(long long limit_cycles, void* stream);
+
 /* Turn the per-launch CUDA-event timing of later solves on (on != 0) or off, whatever
  * opts.profile was at setup.  Errors: EKCG_EINVAL (NULL ctx).                            */
 int ekcg_set_profile(ekcg_ctx* ctx, int on);

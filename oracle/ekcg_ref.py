@@ -16,8 +16,7 @@ partition array directly: T(r)[i, part[i]] = r[i].  The domain permutation of Se
 (rows reordered so that domains are contiguous) is a storage choice; `domain_perm` gives
 the permutation the GPU library must reproduce.
 
-Readings where the paper is silent or refers to the author's thesis (all listed in
-the design doc too):
+Readings where the paper is silent or refers to the author's thesis:
   * CGS2 against Q (thesis Alg. 18, not printed): two passes of C = Q^T (A W),
     W <- W - Q C.  The A-inner products use a fresh sparse product A W of the current W in
     each pass (and one more after the second pass for the Gram matrix below).

@@ -66,12 +66,29 @@ __device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
         : "memory");
     return done != 0;
 }
-// true once the phase with this parity has completed; false after about kWaitCycles
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+// true once the phase with this parity has completed; false after about `limit` cycles
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity,
+                                          long long limit = kWaitCycles) {
     const long long t0 = clock64();
     while (!mbar_test(bar, parity))
-        if (clock64() - t0 > kWaitCycles) return false;
+        if (clock64() - t0 > limit) return false;
     return true;
+}
+
+// Diagnostic of the bounded wait: thread 0 arms an mbarrier for 16 bytes that no copy will
+// deliver, every thread waits at most `limit` cycles, and the CTA sets bit 2 of *err when
+// the wait runs out, the path the staged kernels take on a stage that never completes.
+__global__ void k_wait_selftest(long long limit, int* err) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_barrier_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) mbar_expect_tx(&bar, 16);
+    __syncthreads();
+    const bool ok = mbar_wait(&bar, 0, limit);
+    if (__syncthreads_or(!ok) && threadIdx.x == 0) atomicOr(err, 4);
 }
 
 template <int P, int Q>

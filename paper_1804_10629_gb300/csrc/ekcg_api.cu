@@ -1437,6 +1437,24 @@ int ekcg_last_stats(const ekcg_ctx* c, int64_t* kl, int64_t* sp) {
     return EKCG_OK;
 }
 
+int ekcg_wait_selftest(long long limit_cycles, void* stream) {
+    if (limit_cycles < 1 || limit_cycles > (1ll << 32)) return EKCG_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    int* d = nullptr;
+    int h = 0;
+    if (cudaMalloc(&d, sizeof(int)) != cudaSuccess) return EKCG_ENOMEM;
+    cudaError_t e = cudaMemsetAsync(d, 0, sizeof(int), st);
+    if (e == cudaSuccess) {
+        bulk::k_wait_selftest<<<1, 32, 0, st>>>(limit_cycles, d);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&h, d, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(d);
+    if (e != cudaSuccess) return EKCG_ECUDA;
+    return (h & 4) ? EKCG_ETIMEOUT : EKCG_OK;
+}
+
 int ekcg_set_profile(ekcg_ctx* c, int on) {
     if (!c) return EKCG_EINVAL;
     c->opts.profile = on ? 1 : 0;

@@ -10,7 +10,7 @@ from __future__ import annotations
 import ctypes
 import os
 import re
-from ctypes import POINTER, byref, c_char_p, c_double, c_int, c_int64, c_void_p
+from ctypes import POINTER, byref, c_char_p, c_double, c_int, c_int64, c_longlong, c_void_p
 from typing import Optional
 
 import numpy as np
@@ -67,6 +67,8 @@ def _declare(L):
     L.ekcg_get_perm.restype = c_int
     L.ekcg_last_stats.argtypes = [c_void_p, POINTER(c_int64), POINTER(c_int64)]
     L.ekcg_last_stats.restype = c_int
+    L.ekcg_wait_selftest.argtypes = [c_longlong, c_void_p]
+    L.ekcg_wait_selftest.restype = c_int
     L.ekcg_set_profile.argtypes = [c_void_p, c_int]
     L.ekcg_set_profile.restype = c_int
     L.ekcg_profile.argtypes = [c_void_p, c_int, POINTER(c_char_p), POINTER(c_double),
@@ -213,6 +215,11 @@ def ekcg_last_stats(ctx):
     kl, sp = c_int64(), c_int64()
     lib().ekcg_last_stats(ctx, byref(kl), byref(sp))
     return kl.value, sp.value
+
+
+def ekcg_wait_selftest(limit_cycles, stream=None):
+    """Status of the bounded-wait diagnostic (EKCG_ETIMEOUT when the wait ran out)."""
+    return lib().ekcg_wait_selftest(int(limit_cycles), c_void_p(stream))
 
 
 def ekcg_profile(ctx, cap=32):

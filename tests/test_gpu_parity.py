@@ -364,3 +364,16 @@ def test_sky3d_full_size_against_oracle_record():
     np.testing.assert_allclose(hist[:21], g["hist"][:21], rtol=1e-6)
     assert relres(p.A, p.b, x.cpu().numpy()) <= 1e-8 * 1.01
     S.close()
+
+
+def test_bounded_wait_reports_timeout_and_device_stays_usable():
+    """The bulk-copy stages wait on mbarriers with a cycle limit.  A stage that never
+    completes (16 bytes expected, no copy issued) must end in EKCG_ETIMEOUT, not a hang, and
+    a solve afterwards must still succeed."""
+    assert ekcg.ekcg_wait_selftest(1 << 20) == ekcg.EKCG_ETIMEOUT
+    assert ekcg.ekcg_wait_selftest(0) == ekcg.EKCG_EINVAL
+    A, b, part = ragged_problem(4)
+    S = ekcg.Solver(A, 4, part, max_s=2)
+    x, it, hist, st = S.solve(dev(b), s=2, tol=1e-8, maxit=500)
+    assert st == 0 and relres(A, b, x.cpu().numpy()) <= 1e-8 * 1.01
+    S.close()
