@@ -168,9 +168,11 @@ def cgs2_against_carried(W, AW, Q, AQ):
 # ----------------------------------------------------------------------------------------
 
 class _Ctx:
-    """Per-solve state: the operator, options and bookkeeping."""
+    """Per-solve state: the operator, options, the optional split preconditioner and
+    bookkeeping."""
 
-    def __init__(self, A, part, t, orth, breakdown_tol, explicit_AW, record, carried_cgs=False):
+    def __init__(self, A, part, t, orth, breakdown_tol, explicit_AW, record, carried_cgs=False,
+                 precond=None):
         self.A = A.to_scipy() if hasattr(A, "to_scipy") else sp.csr_matrix(A)
         self.part = np.asarray(part)
         self.t = t
@@ -179,11 +181,26 @@ class _Ctx:
         self.explicit = explicit_AW
         self.carried = carried_cgs
         self.record = record
+        self.pre = precond
         self.spmm = 0
 
     def matmul(self, W):
         self.spmm += 1
         return self.A @ W
+
+    def first_block(self, r):
+        """The block built from a residual: T(r), or with a split preconditioner
+        M = L L^T, L^{-T} T(L^{-1} r) (Section 5, Algorithms 8-10)."""
+        if self.pre is None:
+            return split_T(r, self.part, self.t)
+        return self.pre.solve_LT(split_T(self.pre.solve_L(r), self.part, self.t))
+
+    def candidate(self, AW):
+        """The next block from A W_{j-1}: A W_{j-1} itself, or M^{-1} A W_{j-1} with a
+        split preconditioner (Section 5)."""
+        if self.pre is None:
+            return AW
+        return self.pre.apply(AW)
 
     def self_orth(self, W, AW):
         if self.orth == "acholqr":
@@ -335,15 +352,18 @@ def cg(A, b, x0=None, tol=1e-8, maxit=10000, record=False) -> Result:
 
 def sstep_sre_cg(A, b, part, t, s, tol=1e-8, maxit=1000, x0=None, orth="acholqr",
                  full_history=False, breakdown_tol=1e-14, explicit_AW=False,
-                 record=False, carried_cgs=False) -> Result:
+                 record=False, carried_cgs=False, precond=None) -> Result:
     """s-step SRE-CG (Algorithm 4); with full_history=True, s-step SRE-CG2 (Algorithm 3).
 
     Iteration k builds s blocks W_j..W_{j+s-1}, j = (k-1)s+1.  W_1 = T(r_0) is only
     A-orthonormalised against itself; every later W_j = A W_{j-1} is A-orthonormalised
     against W_{j-2}, W_{j-1} (Alg. 4) or against all previous blocks (Alg. 3), then against
     itself.  Then alpha = V^T r_{k-1}, x_k = x_{k-1} + V alpha, r_k = r_{k-1} - A V alpha.
+    With a split preconditioner M = L L^T (`precond`, Algorithms 8 and 9): W_1 =
+    L^{-T} T(L^{-1} r_0) and W_j = M^{-1} A W_{j-1}; the A-orthonormalisation and the
+    updates are unchanged.
     """
-    ctx = _Ctx(A, part, t, orth, breakdown_tol, explicit_AW, record, carried_cgs)
+    ctx = _Ctx(A, part, t, orth, breakdown_tol, explicit_AW, record, carried_cgs, precond)
     x, r, rho0 = _start(A, b, x0)
     res = Result(x=x, iters=0, hist=[rho0], status=OK)
     _record(ctx, res, x, r)
@@ -358,10 +378,10 @@ def sstep_sre_cg(A, b, part, t, s, tol=1e-8, maxit=1000, x0=None, orth="acholqr"
             Vb = []
             for i in range(s):
                 if k == 1 and i == 0:
-                    W = split_T(r0, ctx.part, t)
+                    W = ctx.first_block(r0)
                     AW = ctx.matmul(W)
                 else:
-                    W = last[1]                            # W_j = A W_{j-1}
+                    W = ctx.candidate(last[1])             # W_j = (M^{-1}) A W_{j-1}
                     AW = ctx.matmul(W)
                     W, AW = ctx.against(W, AW, full if full_history else window)
                 W, AW = ctx.self_orth(W, AW)
@@ -397,11 +417,12 @@ def sstep_sre_cg2(*args, **kw) -> Result:
 
 def sstep_msdo_cg(A, b, part, t, s, tol=1e-8, maxit=1000, x0=None, orth="acholqr",
                   breakdown_tol=1e-14, explicit_AW=False, record=False,
-                  carried_cgs=False) -> Result:
+                  carried_cgs=False, precond=None) -> Result:
     """s-step MSDO-CG (Algorithm 6).  Iteration k: W_1 = T(r_{k-1}) A-orthonormalised
     against Q (k > 1) and itself; W_{i+1} = A W_i against Q and itself, i = 1..s-1; every
-    block joins V and Q.  Then alpha = V^T r_{k-1} and the x / r updates."""
-    ctx = _Ctx(A, part, t, orth, breakdown_tol, explicit_AW, record, carried_cgs)
+    block joins V and Q.  Then alpha = V^T r_{k-1} and the x / r updates.  With a split
+    preconditioner (Algorithm 10): W_1 = L^{-T} T(L^{-1} r_{k-1}), W_{i+1} = M^{-1} A W_i."""
+    ctx = _Ctx(A, part, t, orth, breakdown_tol, explicit_AW, record, carried_cgs, precond)
     x, r, rho0 = _start(A, b, x0)
     res = Result(x=x, iters=0, hist=[rho0], status=OK)
     _record(ctx, res, x, r)
@@ -411,14 +432,14 @@ def sstep_msdo_cg(A, b, part, t, s, tol=1e-8, maxit=1000, x0=None, orth="acholqr
     try:
         while rho > tol * rho0 and k < kmax:
             Vb = []
-            W = split_T(r, ctx.part, t)
+            W = ctx.first_block(r)
             AW = ctx.matmul(W)
             W, AW = ctx.against(W, AW, Qb)
             W, AW = ctx.self_orth(W, AW)
             Vb.append((W, AW))
             Qb.append(W, AW)
             for i in range(1, s):
-                W = Vb[-1][1]                              # W_{i+1} = A W_i
+                W = ctx.candidate(Vb[-1][1])               # W_{i+1} = (M^{-1}) A W_i
                 AW = ctx.matmul(W)
                 W, AW = ctx.against(W, AW, Qb)
                 W, AW = ctx.self_orth(W, AW)
@@ -448,7 +469,7 @@ def _split_blocks(V, AV, t):
 
 def ca_enlarged_cg(A, b, part, t, s, tol=1e-8, maxit=1000, x0=None, orth="acholqr",
                    variant="sre", arnoldi="alg7", breakdown_tol=1e-14, explicit_AW=False,
-                   record=False, carried_cgs=False) -> Result:
+                   record=False, carried_cgs=False, precond=None) -> Result:
     """CA SRE-CG / CA SRE-CG2 / CA MSDO-CG: Algorithms 4 / 3 / 6 with the basis built by
     the CA-Arnoldi A-orthonormalisation (Algorithm 5, arnoldi='alg5') or the modified
     CA-Arnoldi (Algorithm 7, arnoldi='alg7').
@@ -461,10 +482,12 @@ def ca_enlarged_cg(A, b, part, t, s, tol=1e-8, maxit=1000, x0=None, orth="acholq
     (SRE variants); T(r_{k-1}) at every k for MSDO, where W_j = W_{j-1} replaces
     W_j = A W_{j-1} (Section 3.2).
     Q: the last (s+1)t vectors (CA SRE-CG) or all previous vectors (CA SRE-CG2, CA MSDO-CG).
+    With a split preconditioner (Section 5): every A W_{j+i-1} that forms a new block is
+    replaced by M^{-1} A W_{j+i-1}, and the input block T(r) by L^{-T} T(L^{-1} r).
     """
     if variant not in VARIANTS or arnoldi not in ("alg5", "alg7"):
         raise ValueError((variant, arnoldi))
-    ctx = _Ctx(A, part, t, orth, breakdown_tol, explicit_AW, record, carried_cgs)
+    ctx = _Ctx(A, part, t, orth, breakdown_tol, explicit_AW, record, carried_cgs, precond)
     x, r, rho0 = _start(A, b, x0)
     res = Result(x=x, iters=0, hist=[rho0], status=OK)
     _record(ctx, res, x, r)
@@ -479,13 +502,13 @@ def ca_enlarged_cg(A, b, part, t, s, tol=1e-8, maxit=1000, x0=None, orth="acholq
             Qb = window[-(s + 1):] if variant == "sre" else full
             # first block W_j
             if variant == "msdo":
-                Wj = split_T(r, ctx.part, t)
+                Wj = ctx.first_block(r)
                 AWj = ctx.matmul(Wj)
             elif k == 1:
-                Wj = split_T(r0, ctx.part, t)
+                Wj = ctx.first_block(r0)
                 AWj = ctx.matmul(Wj)
             else:
-                Wj = last[1]                               # W_j = A W_{j-1}
+                Wj = ctx.candidate(last[1])                # W_j = (M^{-1}) A W_{j-1}
                 AWj = ctx.matmul(Wj)
             if arnoldi == "alg7":
                 if k > 1:
@@ -493,7 +516,7 @@ def ca_enlarged_cg(A, b, part, t, s, tol=1e-8, maxit=1000, x0=None, orth="acholq
                 Wj, AWj = ctx.self_orth(Wj, AWj)
             Vb = [(Wj, AWj)]
             for i in range(1, s):
-                W = Vb[-1][1]                              # W_{j+i} = A W_{j+i-1}
+                W = ctx.candidate(Vb[-1][1])               # W_{j+i} = (M^{-1}) A W_{j+i-1}
                 Vb.append((W, ctx.matmul(W)))
             V = np.hstack([v[0] for v in Vb])
             AV = np.hstack([v[1] for v in Vb])
@@ -547,10 +570,10 @@ def restructured_sre_cg(A, b, part, t, s, tol=1e-8, maxit=1000, x0=None, orth="a
             Vb = []
             for i in range(s):
                 if k == 1 and i == 0:
-                    W = split_T(r0, ctx.part, t)
+                    W = ctx.first_block(r0)
                     AW = ctx.matmul(W)
                 else:
-                    W = last[1]                            # W_j = A W_{j-1}
+                    W = ctx.candidate(last[1])             # W_j = (M^{-1}) A W_{j-1}
                     AW = ctx.matmul(W)
                     W, AW = ctx.against(W, AW, full if full_history else window)
                 W, AW = ctx.self_orth(W, AW)
@@ -581,18 +604,123 @@ def restructured_sre_cg(A, b, part, t, s, tol=1e-8, maxit=1000, x0=None, orth="a
 
 def solve(A, b, part, t, s, tol=1e-8, maxit=1000, x0=None, variant="sre", basis="sstep",
           orth="acholqr", breakdown_tol=1e-14, explicit_AW=False, record=False,
-          carried_cgs=False) -> Result:
+          carried_cgs=False, precond=None) -> Result:
     """Select the algorithm: basis 'sstep' -> Alg. 4 (sre) / Alg. 3 (sre2) / Alg. 6 (msdo);
-    basis 'ca5' / 'ca7' -> the CA form of the variant with Alg. 5 / Alg. 7."""
+    basis 'ca5' / 'ca7' -> the CA form of the variant with Alg. 5 / Alg. 7.  `precond`
+    (e.g. BlockJacobi) gives the split preconditioned forms of Section 5 (Algorithms 8-10)."""
     if basis == "sstep":
         if variant == "msdo":
             return sstep_msdo_cg(A, b, part, t, s, tol, maxit, x0, orth, breakdown_tol,
-                                 explicit_AW, record, carried_cgs)
+                                 explicit_AW, record, carried_cgs, precond)
         return sstep_sre_cg(A, b, part, t, s, tol, maxit, x0, orth, variant == "sre2",
-                            breakdown_tol, explicit_AW, record, carried_cgs)
+                            breakdown_tol, explicit_AW, record, carried_cgs, precond)
     return ca_enlarged_cg(A, b, part, t, s, tol, maxit, x0, orth, variant,
                           "alg5" if basis == "ca5" else "alg7", breakdown_tol, explicit_AW,
-                          record, carried_cgs)
+                          record, carried_cgs, precond)
+
+
+# ----------------------------------------------------------------------------------------
+# Split preconditioning (Section 5): block Jacobi M = L L^T, preconditioned CG
+# ----------------------------------------------------------------------------------------
+
+def ic0(Ad: np.ndarray) -> np.ndarray:
+    """Incomplete Cholesky factor with zero fill-in of a dense SPD block: the lower
+    triangular L with the sparsity pattern of tril(Ad), computed by the right-looking
+    Cholesky elimination in which every update that falls outside the pattern is dropped
+    (so (L L^T)_ij = Ad_ij on the pattern)."""
+    n = Ad.shape[0]
+    S = Ad != 0
+    a = np.tril(np.asarray(Ad, dtype=np.float64)).copy()
+    for k in range(n):
+        if not (a[k, k] > 0):
+            raise Breakdown(f"ic0 pivot {k}")
+        a[k, k] = math.sqrt(a[k, k])
+        rows = k + 1 + np.nonzero(S[k + 1:, k])[0]
+        a[rows, k] /= a[k, k]
+        for j in rows:
+            ii = rows[rows >= j]
+            ii = ii[S[ii, j]]
+            a[ii, j] -= a[ii, k] * a[j, k]
+    return a
+
+
+class BlockJacobi:
+    """Block Jacobi preconditioner M = L L^T of the preconditioned experiments of Section
+    5: L is block diagonal over the domains of `bpart` (each row in one block), and L_i is
+    the lower factor of the diagonal block A(D_i, D_i), either its complete Cholesky factor
+    (factor='cholesky') or its incomplete Cholesky factor with zero fill-in (factor='ic0').
+    solve_L / solve_LT / apply act on vectors or n x m blocks."""
+
+    def __init__(self, A, bpart, factor="cholesky"):
+        As = A.to_scipy() if hasattr(A, "to_scipy") else sp.csr_matrix(A)
+        bpart = np.asarray(bpart)
+        self.n = As.shape[0]
+        self.blocks = []
+        for d in np.unique(bpart):
+            idx = np.nonzero(bpart == d)[0]
+            Ad = As[idx][:, idx].toarray()
+            if factor == "cholesky":
+                L = sla.cholesky(Ad, lower=True)
+            elif factor == "ic0":
+                L = ic0(Ad)
+            else:
+                raise ValueError(factor)
+            self.blocks.append((idx, L))
+
+    def solve_L(self, X):
+        Y = np.array(X, dtype=np.float64, copy=True)
+        for idx, L in self.blocks:
+            Y[idx] = sla.solve_triangular(L, Y[idx], lower=True)
+        return Y
+
+    def solve_LT(self, X):
+        Y = np.array(X, dtype=np.float64, copy=True)
+        for idx, L in self.blocks:
+            Y[idx] = sla.solve_triangular(L, Y[idx], lower=True, trans="T")
+        return Y
+
+    def apply(self, X):
+        """M^{-1} X = L^{-T} L^{-1} X."""
+        return self.solve_LT(self.solve_L(X))
+
+    def L_dense(self):
+        """The block diagonal factor L as a dense matrix (small test problems)."""
+        L = np.zeros((self.n, self.n))
+        for idx, Li in self.blocks:
+            L[np.ix_(idx, idx)] = Li
+        return L
+
+
+def pcg(A, b, precond, x0=None, tol=1e-8, maxit=10000, record=False) -> Result:
+    """Preconditioned CG as stated at the end of Section 6: p_1 = M^{-1} r_0,
+    p_k = M^{-1} r_{k-1} + beta p_{k-1}, beta = rhat_{k-1} / rhat_{k-2} with
+    rhat_k = r_k^T M^{-1} r_k, alpha = rhat_{k-1} / p^T A p, x_k = x_{k-1} + alpha p,
+    r_k = r_{k-1} - alpha A p; stopping rule on ||r_k||_2 as for CG."""
+    Asp = A.to_scipy() if hasattr(A, "to_scipy") else sp.csr_matrix(A)
+    x, r, rho0 = _start(A, b, x0)
+    res = Result(x=x, iters=0, hist=[rho0], status=OK)
+    if record:
+        res.xs.append(x.copy())
+    z = precond.apply(r)
+    rz = float(r @ z)
+    rho, k = rho0, 1
+    p = None
+    rz_prev = None
+    kmax = maxit + 1
+    while rho > tol * rho0 and k < kmax:
+        p = z.copy() if k == 1 else z + (rz / rz_prev) * p
+        w = Asp @ p
+        alpha = rz / float(p @ w)
+        x = x + alpha * p
+        r = r - alpha * w
+        z = precond.apply(r)
+        rz_prev, rz = rz, float(r @ z)
+        rho = float(np.linalg.norm(r))
+        res.hist.append(rho)
+        if record:
+            res.xs.append(x.copy())
+        k += 1
+    return _finish(res, x, rho, rho0, tol, k)
 
 
 # ----------------------------------------------------------------------------------------
