@@ -52,6 +52,8 @@ extern "C" {
 #define EKCG_SSTEP 0  /* basis built t vectors at a time (Algorithms 3, 4, 6)             */
 #define EKCG_CA5 1    /* CA-Arnoldi A-orthonormalisation (Algorithm 5, monomial, unstable) */
 #define EKCG_CA7 2    /* modified CA-Arnoldi A-orthonormalisation (Algorithm 7)           */
+#define EKCG_RESTRUCT 3 /* restructured SRE-CG / SRE-CG2 (Algorithms 2, 1): the s-step basis,
+                         * then s sequential updates, one per block (SRE and SRE2 only)    */
 
 #define EKCG_ACHOLQR 0    /* A-CholQR: G = W^T A W = R^T R, W <- W R^{-1}                 */
 #define EKCG_PRECHOLQR 1  /* Euclidean CholQR2 first, then A-CholQR                       */
@@ -63,7 +65,7 @@ typedef struct ekcg_ctx ekcg_ctx;
 
 typedef struct {
     int variant;          /* EKCG_SRE / EKCG_SRE2 / EKCG_MSDO                            */
-    int basis;            /* EKCG_SSTEP / EKCG_CA5 / EKCG_CA7                            */
+    int basis;            /* EKCG_SSTEP / EKCG_CA5 / EKCG_CA7 / EKCG_RESTRUCT            */
     int orth;             /* EKCG_ACHOLQR / EKCG_PRECHOLQR                                */
     int precision;        /* EKCG_FP64 / EKCG_FP32_IR                                     */
     int max_s;            /* largest s any solve on this context uses (workspace size)     */

@@ -607,7 +607,13 @@ def solve(A, b, part, t, s, tol=1e-8, maxit=1000, x0=None, variant="sre", basis=
           carried_cgs=False, precond=None) -> Result:
     """Select the algorithm: basis 'sstep' -> Alg. 4 (sre) / Alg. 3 (sre2) / Alg. 6 (msdo);
     basis 'ca5' / 'ca7' -> the CA form of the variant with Alg. 5 / Alg. 7.  `precond`
-    (e.g. BlockJacobi) gives the split preconditioned forms of Section 5 (Algorithms 8-10)."""
+    (e.g. BlockJacobi) gives the split preconditioned forms of Section 5 (Algorithms 8-10).
+    basis 'restructured' -> Alg. 2 (sre) / Alg. 1 (sre2)."""
+    if basis == "restructured":
+        if variant == "msdo" or precond is not None:
+            raise ValueError("the restructured forms are Algorithms 1 and 2 (SRE-CG, SRE-CG2)")
+        return restructured_sre_cg(A, b, part, t, s, tol, maxit, x0, orth, variant == "sre2",
+                                   breakdown_tol, record, carried_cgs)
     if basis == "sstep":
         if variant == "msdo":
             return sstep_msdo_cg(A, b, part, t, s, tol, maxit, x0, orth, breakdown_tol,

@@ -678,7 +678,7 @@ struct Engine {
         : c(ctx), s(s_), t(ctx->t), n(ctx->n), slot(ctx->n * ctx->t), Wb(Arena<T>::W(ctx)),
           Zb(Arena<T>::Z(ctx)), x(x_), r(r_) {
         const int v = c->opts.variant, bs = c->opts.basis;
-        if (bs == EKCG_SSTEP)
+        if (bs == EKCG_SSTEP || bs == EKCG_RESTRUCT)
             ring = (v == EKCG_SRE) ? s + 2 : c->nslots;
         else
             ring = (v == EKCG_SRE) ? 2 * s + 1 : c->nslots;
@@ -840,17 +840,18 @@ struct Engine {
         return EKCG_OK;
     }
 
-    // alpha = V^T r, x += V alpha, r -= (A V) alpha, rho = ||r||.
-    int update(int64_t v0) {
-        EK_TRY((run_gram<T, double, double>(c, as_const(Wm(v0, s)), mb<const T>(r, 0, 0, 1, 1, 1),
-                                            c->alpha, c->partials)));
+    // alpha = V^T r for the nb blocks of V starting at block v0, then x += V alpha,
+    // r -= (A V) alpha and the CTA partials of ||r||^2.
+    int block_update(int64_t v0, int nb) {
+        const MB<const T> V = as_const(Wm(v0, nb)), AV = as_const(Zm(v0, nb));
+        EK_TRY((run_gram<T, double, double>(c, V, mb<const T>(r, 0, 0, 1, 1, 1), c->alpha,
+                                            c->partials)));
         {
-            const double nn = (double)n, stc = (double)s * t;
+            const double nn = (double)n, stc = (double)nb * t;
             Launch L(c, KC_XR, 4.0 * nn * stc + 2.0 * nn, nn * (2.0 * stc + 4.0) * sizeof(T));
-            const MB<const T> V = as_const(Wm(v0, s)), AV = as_const(Zm(v0, s));
             const int g4 = t / 4;
             const bool f32_rows = std::is_same<T, float>::value && t % 4 == 0 && g4 <= 32 &&
-                                  (g4 & (g4 - 1)) == 0 && s * t <= kMaxAlpha &&
+                                  (g4 & (g4 - 1)) == 0 && nb * t <= kMaxAlpha &&
                                   ((uintptr_t)V.base % 16) == 0 && V.stride % 4 == 0 &&
                                   ((uintptr_t)AV.base % 16) == 0 && AV.stride % 4 == 0;
             if constexpr (std::is_same<T, float>::value) {
@@ -862,12 +863,28 @@ struct Engine {
                 k_xr_update<T><<<c->grid_red, kThreads, 0, c->stream>>>(x, r, V, AV, c->alpha, n,
                                                                         c->red, c->flag);
         }
-        EK_TRY(check_launch("k_xr_update"));
+        return check_launch("k_xr_update");
+    }
+
+    int finish_norm() {
         {
             Launch L(c, KC_NORM);
             k_norm_finalize<<<1, 32, 0, c->stream>>>(c->red, c->grid_red, c->rho);
         }
         return check_launch("k_norm_finalize");
+    }
+
+    // alpha = V^T r, x += V alpha, r -= (A V) alpha, rho = ||r|| (Algorithms 3, 4, 6).
+    int update(int64_t v0) {
+        EK_TRY(block_update(v0, s));
+        return finish_norm();
+    }
+
+    // Restructured forms (Algorithms 1, 2): for i = 1..s, alpha_i = W_i^T r_{i-1},
+    // x_i = x_{i-1} + W_i alpha_i, r_i = r_{i-1} - A W_i alpha_i; rho = ||r|| after the s-th.
+    int update_restructured(int64_t v0) {
+        for (int i = 0; i < s; ++i) EK_TRY(block_update(v0 + i, 1));
+        return finish_norm();
     }
 };
 
@@ -916,10 +933,13 @@ int sstep_loop(ekcg_ctx* c, int s, double tol_abs, int maxit, T* x, T* r, double
     while (rho > tol_abs && k < maxit + 1 &&
            !(stag > 0 && k - 1 - k_best >= std::max(stag, k_best / 2))) {
         int64_t v0 = 0;
-        int rc = (c->opts.basis == EKCG_SSTEP) ? E.iterate_sstep(k, r, &v0)
-                                               : E.iterate_ca(k, r, &v0);
+        const bool sstep_basis = c->opts.basis == EKCG_SSTEP || c->opts.basis == EKCG_RESTRUCT;
+        int rc = sstep_basis ? E.iterate_sstep(k, r, &v0) : E.iterate_ca(k, r, &v0);
         if (rc != EKCG_OK) return rc;
-        EK_TRY(E.update(v0));
+        if (c->opts.basis == EKCG_RESTRUCT)
+            EK_TRY(E.update_restructured(v0));
+        else
+            EK_TRY(E.update(v0));
         EK_TRY(sync_read(c, &rho, &flag));
         if (flag & 4) {
             set_error("ekcg_solve", "a staged bulk copy did not complete within its wait limit");
@@ -1071,7 +1091,8 @@ int alloc_workspace(ekcg_ctx* c) {
     const bool full = c->opts.variant != EKCG_SRE;
     int nslots;
     if (!full) {
-        nslots = (c->opts.basis == EKCG_SSTEP) ? S + 2 : 2 * S + 1;
+        nslots = (c->opts.basis == EKCG_SSTEP || c->opts.basis == EKCG_RESTRUCT) ? S + 2
+                                                                                 : 2 * S + 1;
     } else if (c->opts.max_blocks > 0) {
         nslots = c->opts.max_blocks;
     } else {
@@ -1333,7 +1354,8 @@ int ekcg_setup(int64_t n, const int64_t* rowptr, const int32_t* colind, const do
     else
         ekcg_default_opts(&c->opts);
     const ekcg_opts& o = c->opts;
-    if (o.variant < 0 || o.variant > 2 || o.basis < 0 || o.basis > 2 || o.orth < 0 ||
+    if (o.variant < 0 || o.variant > 2 || o.basis < 0 || o.basis > 3 ||
+        (o.basis == EKCG_RESTRUCT && o.variant == EKCG_MSDO) || o.orth < 0 ||
         o.orth > 1 || o.precision < 0 || o.precision > 1 || o.max_s < 1 ||
         o.max_s * t > kPMax || o.max_blocks < 0 || !(o.breakdown_tol >= 0) ||
         !(o.inner_tol > 0 && o.inner_tol < 1) || o.max_refine < 1) {

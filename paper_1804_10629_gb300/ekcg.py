@@ -22,7 +22,7 @@ HEADER = os.path.join(os.path.dirname(HERE), "include", "ekcg.h")
 EKCG_OK, EKCG_MAXIT, EKCG_EINVAL, EKCG_ENOMEM, EKCG_EBREAKDOWN, EKCG_ETIMEOUT, EKCG_ECUDA = \
     0, 1, -1, -2, -3, -4, -5
 VARIANT = {"sre": 0, "sre2": 1, "msdo": 2}
-BASIS = {"sstep": 0, "ca5": 1, "ca7": 2}
+BASIS = {"sstep": 0, "ca5": 1, "ca7": 2, "restructured": 3}
 ORTH = {"acholqr": 0, "precholqr": 1}
 PRECISION = {"fp64": 0, "fp32_ir": 1}
 

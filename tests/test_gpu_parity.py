@@ -144,6 +144,21 @@ def test_solver_parity_ragged(variant, basis, s):
     check_parity(A, b, part, 4, s, variant, basis)
 
 
+@pytest.mark.parametrize("variant", ["sre", "sre2"])
+@pytest.mark.parametrize("s", [1, 2, 3])
+def test_restructured_parity(variant, s):
+    """Restructured SRE-CG / SRE-CG2 (Algorithms 2 / 1): the s-step basis, then s sequential
+    block updates per outer iteration, against the oracle's restructured form."""
+    A, b, part = ragged_problem()
+    check_parity(A, b, part, 4, s, variant, "restructured")
+
+
+def test_restructured_msdo_is_rejected():
+    A, b, part = ragged_problem()
+    with pytest.raises(Exception):
+        ekcg.Solver(A, 4, part, variant="msdo", basis="restructured", max_s=2)
+
+
 @pytest.mark.parametrize("variant", ["sre", "sre2", "msdo"])
 def test_precholqr_parity(variant):
     A, b, part = ragged_problem(t=8)

@@ -480,3 +480,18 @@ def test_paper_poisson2d_iteration_counts(m, t, s, c):
         got = o.solve(A, b, part, t, s, tol=1e-6, maxit=1000, variant=m).iters
         band = 0.08 if m == "msdo" else 0.05
     assert abs(got - c) <= band * c, (m, t, s, c, got)
+
+
+def test_restructured_dispatch_matches_direct_call():
+    """solve(basis='restructured') is Algorithm 2 (sre) / Algorithm 1 (sre2); MSDO-CG and
+    preconditioning have no restructured form in the paper and are rejected."""
+    A = wl.stencil_matrix((14, 11))
+    part = wl.partition_boxes((14, 11), 4)
+    b = wl.rhs_uniform(A.n, 3)
+    for variant in ("sre", "sre2"):
+        r1 = o.solve(A, b, part, 4, 3, tol=1e-10, variant=variant, basis="restructured")
+        r2 = o.restructured_sre_cg(A, b, part, 4, 3, tol=1e-10,
+                                   full_history=(variant == "sre2"))
+        assert r1.iters == r2.iters and np.array_equal(r1.x, r2.x)
+    with pytest.raises(ValueError):
+        o.solve(A, b, part, 4, 2, variant="msdo", basis="restructured")
