@@ -138,6 +138,29 @@ int ekcg_get_perm(const ekcg_ctx* ctx, int64_t* perm);
 /* Kernel launches and sparse products of the last solve.                                 */
 int ekcg_last_stats(const ekcg_ctx* ctx, int64_t* kernel_launches, int64_t* spmm_calls);
 
+/* Block Jacobi split preconditioner M = L L^T of Section 5 (Algorithms 8-10) for later
+ * solves: L is block diagonal over the blocks of bpart (host array of n block ids in
+ * [0, nblocks), natural row order, copied), each diagonal block factored by incomplete
+ * Cholesky with zero fill-in, computed on the host in the library's row order (within a
+ * block the natural order).  Every block must lie inside one of the t domains (the paper's
+ * blocks are subdomains of the t domains).  The s-step solves then build the first block as
+ * L^{-T} T(L^{-1} r) and every later candidate as M^{-1} A W_{j-1}.  bpart = NULL removes
+ * the preconditioner.  Float64 precision and the s-step basis (EKCG_SSTEP) only.
+ * Errors: EKCG_EINVAL (ids out of range, a block across two domains, IC(0) breakdown,
+ * other precision or basis), EKCG_ENOMEM, EKCG_ECUDA.                                    */
+int ekcg_set_block_jacobi(ekcg_ctx* ctx, const int32_t* bpart, int nblocks);
+
+/* Host-only inspection of the preconditioner setup (no device work, no context): for the
+ * CSR matrix (n, rowptr, colind sorted per row, val) and block ids bpart[n] in [0, nblocks)
+ * with the rows in the given order, the IC(0) factor of every diagonal block and the solve
+ * levels, as computed by ekcg_set_block_jacobi.  lval[nnz] (caller-owned) receives L_ik for
+ * every stored (i, k) with k < i in the same block, L_ii on the diagonal and 0 elsewhere;
+ * fwd_level[n] / bwd_level[n] the level of each row in the L and L^T solves.
+ * Errors: EKCG_EINVAL (bad CSR, ids out of range, IC(0) breakdown).                       */
+int ekcg_block_ic0_host(int64_t n, const int64_t* rowptr, const int32_t* colind,
+                        const double* val, const int32_t* bpart, int nblocks, double* lval,
+                        int32_t* fwd_level, int32_t* bwd_level);
+
 /* Diagnostic, no counterpart in the paper: runs the bounded mbarrier wait of the
  * bulk-copy-staged kernels on a stage that never completes (16 bytes expected, no copy
  * issued), with a limit of limit_cycles SM cycles (1 .. 2^32), on `stream` (NULL = default

@@ -17,6 +17,7 @@
 #include "../../include/ekcg.h"
 #include "kernels.cuh"
 #include "bulk.cuh"
+#include "precond.cuh"
 
 using namespace ekcg;
 
@@ -45,13 +46,13 @@ void set_error(const char* where, const char* what) {
 
 enum KClass {
     KC_SPMM = 0, KC_GRAM, KC_REDUCE, KC_UPDATE, KC_CHOL, KC_XR, KC_RESID, KC_SPLIT, KC_PERM,
-    KC_COPY, KC_NORM, KC_MISC, KC_GRAM_DF, KC_COUNT
+    KC_COPY, KC_NORM, KC_MISC, KC_GRAM_DF, KC_PRECOND, KC_COUNT
 };
 // gram_df: the float-float upper-triangle Gram of the float32 path (FP32-pipe bound; its
 // operation count is 10 FP32 operations per multiply-add)
 const char* kClassNames[KC_COUNT] = {"spmm", "gram", "gram_reduce", "block_update", "chol_inv",
                                      "xr_update", "residual", "split_T", "permute", "copy",
-                                     "norm", "misc", "gram_df"};
+                                     "norm", "misc", "gram_df", "precond"};
 
 }  // namespace
 
@@ -104,6 +105,16 @@ struct ekcg_ctx {
     int* flag = nullptr;           // bit 0: Cholesky breakdown
     double* h_pinned = nullptr;    // pinned host: rho
     int* h_flag = nullptr;         // pinned host: flag
+
+    // block Jacobi preconditioner, IC(0) blocks (Section 5); bj_nblk = 0: none.  Forward
+    // (L) and backward (L^T) solves: per-row CSR of the off-diagonal entries, level lists.
+    int bj_nblk = 0;
+    int32_t *bj_frp = nullptr, *bj_fci = nullptr, *bj_fblk = nullptr, *bj_flev = nullptr,
+            *bj_frows = nullptr;
+    int32_t *bj_brp = nullptr, *bj_bci = nullptr, *bj_bblk = nullptr, *bj_blev = nullptr,
+            *bj_brows = nullptr;
+    double *bj_fv = nullptr, *bj_bv = nullptr, *bj_diag = nullptr;
+    double* bj_vec = nullptr;      // n-vector scratch: L^{-1} r
 
     int grid_rows = 0;             // row CTAs of the Gram kernel
     int grid_red = 0;              // CTAs of norm-producing kernels
@@ -222,6 +233,20 @@ int run_split(ekcg_ctx* c, const T* r, T* out) {
     k_split_T<T><<<grid_for(c, c->n * c->t), kThreads, 0, c->stream>>>(out, r, c->dom, c->n,
                                                                       c->t);
     return check_launch("k_split_T");
+}
+
+// X <- L^{-1} X (forward) or L^{-T} X (backward) with the block Jacobi IC(0) factor; X is
+// n x w (permuted rows).  One CTA per block, levels in order (precond.cuh).
+int run_bj_trsv(ekcg_ctx* c, double* X, int w, bool forward) {
+    const double flops = 2.0 * (double)w * (double)c->n;   // diagonal; off-diagonal below
+    Launch L(c, KC_PRECOND, flops, 16.0 * (double)c->n * w);
+    if (forward)
+        k_bj_trsv<<<c->bj_nblk, 256, 0, c->stream>>>(X, w, c->bj_fblk, c->bj_flev, c->bj_frows,
+                                                     c->bj_frp, c->bj_fci, c->bj_fv, c->bj_diag);
+    else
+        k_bj_trsv<<<c->bj_nblk, 256, 0, c->stream>>>(X, w, c->bj_bblk, c->bj_blev, c->bj_brows,
+                                                     c->bj_brp, c->bj_bci, c->bj_bv, c->bj_diag);
+    return check_launch("k_bj_trsv");
 }
 
 // C[c_row0 + p, q] (ldc) = (X^T Y)[p, q]; X is chunked by the caller to <= kPMax columns.
@@ -757,6 +782,29 @@ struct Engine {
         }
     }
 
+    // T(r), or L^{-T} T(L^{-1} r) with the block Jacobi preconditioner, into Wj.
+    int first_block(const T* rv, T* Wj) {
+        if constexpr (std::is_same<T, double>::value) {
+            if (c->bj_nblk > 0) {
+                EK_TRY(run_copy<T>(c, c->bj_vec, rv, n));
+                EK_TRY(run_bj_trsv(c, c->bj_vec, 1, true));
+                EK_TRY(run_split<T>(c, c->bj_vec, Wj));
+                return run_bj_trsv(c, Wj, t, false);
+            }
+        }
+        return run_split<T>(c, rv, Wj);
+    }
+
+    // Wj <- M^{-1} Wj = L^{-T} L^{-1} Wj (block Jacobi, float64 path only).
+    int precondition(T* Wj) {
+        if constexpr (std::is_same<T, double>::value) {
+            EK_TRY(run_bj_trsv(c, Wj, t, true));
+            return run_bj_trsv(c, Wj, t, false);
+        }
+        set_error("solve", "block Jacobi preconditioning runs in float64 only");
+        return EKCG_EINVAL;
+    }
+
     // Iteration k (1-based) of Algorithms 3 / 4 / 6; returns the first block of V.
     int iterate_sstep(int k, const T* r0_for_T, int64_t* v0) {
         const int v = c->opts.variant;
@@ -769,10 +817,20 @@ struct Engine {
         for (int i = 0; i < s; ++i) {
             const int64_t j = j0 + i;
             if ((v == EKCG_MSDO && i == 0) || (v != EKCG_MSDO && j == 0)) {
-                // W = T(r_{k-1}) (MSDO, against all previous blocks) or T(r_0)
-                EK_TRY(run_split<T>(c, v == EKCG_MSDO ? r : r0_for_T, W(j)));
+                // W = T(r_{k-1}) (MSDO, against all previous blocks) or T(r_0); with the
+                // block Jacobi preconditioner L^{-T} T(L^{-1} r) (Algorithms 8-10)
+                EK_TRY(first_block(v == EKCG_MSDO ? r : r0_for_T, W(j)));
                 EK_TRY(run_spmm<T>(c, W(j), Z(j), t));
                 EK_TRY(cgs2(j, 1, 0, v == EKCG_MSDO ? (int)j : 0, nullptr));
+            } else if (c->bj_nblk > 0) {
+                // W_j = M^{-1} A W_{j-1}, from the product carried with the previous block
+                EK_TRY(run_copy<T>(c, W(j), Z(j - 1), slot));
+                EK_TRY(precondition(W(j)));
+                EK_TRY(run_spmm<T>(c, W(j), Z(j), t));
+                int64_t q0;
+                int qc;
+                window(j, &q0, &qc);
+                EK_TRY(cgs2(j, 1, q0, qc, nullptr));
             } else {
                 // W_j = A W_{j-1}: the product carried with the previous block
                 const T* cand = Z(j - 1);
@@ -1155,6 +1213,18 @@ int alloc_workspace(ekcg_ctx* c) {
     return EKCG_OK;
 }
 
+void free_block_jacobi(ekcg_ctx* c) {
+    void* ptrs[] = {c->bj_frp, c->bj_fci, c->bj_fblk, c->bj_flev, c->bj_frows, c->bj_brp,
+                    c->bj_bci, c->bj_bblk, c->bj_blev, c->bj_brows, c->bj_fv, c->bj_bv,
+                    c->bj_diag, c->bj_vec};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    c->bj_frp = c->bj_fci = c->bj_fblk = c->bj_flev = c->bj_frows = nullptr;
+    c->bj_brp = c->bj_bci = c->bj_bblk = c->bj_blev = c->bj_brows = nullptr;
+    c->bj_fv = c->bj_bv = c->bj_diag = c->bj_vec = nullptr;
+    c->bj_nblk = 0;
+}
+
 void free_ctx(ekcg_ctx* c) {
     void* ptrs[] = {c->rowptr, c->col, c->val, c->val32, c->perm, c->dom, c->nzmap,
                     c->nat_rowptr, c->W64, c->Z64,
@@ -1163,6 +1233,7 @@ void free_ctx(ekcg_ctx* c) {
                     c->Rinv, c->Rinv32, c->alpha, c->rho, c->flag};
     for (void* p : ptrs)
         if (p) cudaFree(p);
+    free_block_jacobi(c);
     if (c->h_pinned) cudaFreeHost(c->h_pinned);
     if (c->h_flag) cudaFreeHost(c->h_flag);
     for (auto e : c->ev_pool) cudaEventDestroy(e);
@@ -1322,6 +1393,114 @@ int solve_device(ekcg_ctx* c, const double* b, const double* x0, int s, double t
 // ---------------------------------------------------------------------------------------
 // Exported entry points
 // ---------------------------------------------------------------------------------------
+namespace {
+
+// Host part of the block Jacobi preconditioner: the IC(0) factor of every diagonal block
+// (rows taken in the given order; pb[i] = block of row i) and the level schedules of the
+// forward (L) and backward (L^T) solves.  rp / col / val: CSR with sorted columns.
+struct BJHost {
+    std::vector<int32_t> lrp, lci, urp, uci, flev, blev, fblk, flv, frows, bblk, blv, brows;
+    std::vector<double> lv, uv, diag;
+};
+
+int bj_build_host(int64_t n, const int32_t* rp, const int32_t* col, const double* val,
+                  const int32_t* pb, int nblocks, BJHost* H, std::string* err) {
+    auto& lrp = H->lrp;
+    auto& lci = H->lci;
+    auto& lv = H->lv;
+    auto& diag = H->diag;
+    // IC(0), row by row: L_ik = (a_ik - sum_{j<k} L_ij L_kj) / L_kk over the strictly lower
+    // entries of row i inside its block, L_ii = sqrt(a_ii - sum_k L_ik^2); entries outside
+    // tril(A) stay zero, so (L L^T)_ik = a_ik on the pattern.
+    lrp.assign(n + 1, 0);
+    lci.clear();
+    lv.clear();
+    diag.assign(n, 0.0);
+    for (int64_t i = 0; i < n; ++i) {
+        double aii = 0.0;
+        for (int32_t e = rp[i]; e < rp[i + 1]; ++e) {
+            const int32_t k = col[e];
+            if (k < i && pb[k] == pb[i]) {
+                lci.push_back(k);
+                lv.push_back(val[e]);
+            } else if (k == i) {
+                aii = val[e];
+            }
+        }
+        lrp[i + 1] = (int32_t)lci.size();
+        for (int32_t a = lrp[i]; a < lrp[i + 1]; ++a) {
+            const int32_t k = lci[a];
+            double sum = lv[a];
+            int32_t p = lrp[i], q = lrp[k];
+            while (p < a && q < lrp[k + 1]) {       // j < k in both rows i and k
+                if (lci[p] == lci[q]) {
+                    sum -= lv[p] * lv[q];
+                    ++p;
+                    ++q;
+                } else if (lci[p] < lci[q]) {
+                    ++p;
+                } else {
+                    ++q;
+                }
+            }
+            lv[a] = sum / diag[k];
+        }
+        double d = aii;
+        for (int32_t a = lrp[i]; a < lrp[i + 1]; ++a) d -= lv[a] * lv[a];
+        if (!(d > 0.0) || !std::isfinite(d)) {
+            *err = "IC(0) breakdown (non-positive pivot)";
+            return EKCG_EINVAL;
+        }
+        diag[i] = std::sqrt(d);
+    }
+    // L^T stored row-wise: row k holds (i, L_ik) for the rows i > k that read it
+    auto& urp = H->urp;
+    auto& uci = H->uci;
+    auto& uv = H->uv;
+    urp.assign(n + 1, 0);
+    uci.assign(lci.size(), 0);
+    uv.assign(lci.size(), 0.0);
+    for (int32_t k : lci) urp[k + 1]++;
+    for (int64_t i = 0; i < n; ++i) urp[i + 1] += urp[i];
+    {
+        std::vector<int32_t> pos(urp.begin(), urp.end() - 1);
+        for (int64_t i = 0; i < n; ++i)
+            for (int32_t a = lrp[i]; a < lrp[i + 1]; ++a) {
+                uci[pos[lci[a]]] = (int32_t)i;
+                uv[pos[lci[a]]++] = lv[a];
+            }
+    }
+    // levels: forward in increasing row order, backward in decreasing row order
+    auto& flev = H->flev;
+    auto& blev = H->blev;
+    flev.assign(n, 0);
+    blev.assign(n, 0);
+    for (int64_t i = 0; i < n; ++i)
+        for (int32_t a = lrp[i]; a < lrp[i + 1]; ++a) flev[i] = std::max(flev[i], flev[lci[a]] + 1);
+    for (int64_t i = n - 1; i >= 0; --i)
+        for (int32_t a = urp[i]; a < urp[i + 1]; ++a) blev[i] = std::max(blev[i], blev[uci[a]] + 1);
+    // rows grouped by (block, level): blk[d] .. blk[d+1] level indices, lev[l] .. lev[l+1]
+    auto group = [&](const std::vector<int32_t>& lv_of, std::vector<int32_t>& blk,
+                     std::vector<int32_t>& lev, std::vector<int32_t>& rows) {
+        std::vector<int32_t> nlev(nblocks, 0);
+        for (int64_t i = 0; i < n; ++i) nlev[pb[i]] = std::max(nlev[pb[i]], lv_of[i] + 1);
+        blk.assign(nblocks + 1, 0);
+        for (int d = 0; d < nblocks; ++d) blk[d + 1] = blk[d] + nlev[d];
+        std::vector<int32_t> cnt(blk[nblocks] + 1, 0);
+        for (int64_t i = 0; i < n; ++i) cnt[blk[pb[i]] + lv_of[i] + 1]++;
+        for (int l = 0; l < blk[nblocks]; ++l) cnt[l + 1] += cnt[l];
+        lev = cnt;
+        rows.assign(n, 0);
+        std::vector<int32_t> pos(cnt.begin(), cnt.end() - 1);
+        for (int64_t i = 0; i < n; ++i) rows[pos[blk[pb[i]] + lv_of[i]]++] = (int32_t)i;
+    };
+    group(flev, H->fblk, H->flv, H->frows);
+    group(blev, H->bblk, H->blv, H->brows);
+    return EKCG_OK;
+}
+
+}  // namespace
+
 extern "C" {
 
 void ekcg_default_opts(ekcg_opts* o) {
@@ -1456,6 +1635,133 @@ int ekcg_last_stats(const ekcg_ctx* c, int64_t* kl, int64_t* sp) {
     if (!c) return EKCG_EINVAL;
     if (kl) *kl = c->launches;
     if (sp) *sp = c->spmm_calls;
+    return EKCG_OK;
+}
+
+int ekcg_set_block_jacobi(ekcg_ctx* c, const int32_t* bpart, int nblocks) {
+    if (!c) return EKCG_EINVAL;
+    EK_CUDA(cudaStreamSynchronize(c->stream));
+    free_block_jacobi(c);
+    if (!bpart) return EKCG_OK;
+    if (nblocks < 1 || c->opts.precision != EKCG_FP64 || c->opts.basis != EKCG_SSTEP) {
+        set_error("ekcg_set_block_jacobi",
+                  "needs nblocks >= 1, float64 precision and the s-step basis");
+        return EKCG_EINVAL;
+    }
+    const int64_t n = c->n;
+    // the permuted matrix and domains, back on the host
+    std::vector<int32_t> rp(n + 1), dom(n);
+    EK_CUDA(cudaMemcpy(rp.data(), c->rowptr, (n + 1) * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    EK_CUDA(cudaMemcpy(dom.data(), c->dom, n * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    std::vector<int32_t> col(rp[n]);
+    std::vector<double> val(rp[n]);
+    EK_CUDA(cudaMemcpy(col.data(), c->col, rp[n] * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    EK_CUDA(cudaMemcpy(val.data(), c->val, rp[n] * sizeof(double), cudaMemcpyDeviceToHost));
+    // block of every permuted row; every block inside one of the t domains
+    std::vector<int32_t> pb(n);
+    std::vector<int32_t> bdom(nblocks, -1);
+    for (int64_t i = 0; i < n; ++i) {
+        const int32_t b = bpart[c->perm_h[i]];
+        if (b < 0 || b >= nblocks) {
+            set_error("ekcg_set_block_jacobi", "block id out of range");
+            return EKCG_EINVAL;
+        }
+        if (bdom[b] < 0) bdom[b] = dom[i];
+        if (bdom[b] != dom[i]) {
+            set_error("ekcg_set_block_jacobi", "a block spans two of the t domains");
+            return EKCG_EINVAL;
+        }
+        pb[i] = b;
+    }
+    BJHost H;
+    std::string berr;
+    if (bj_build_host(n, rp.data(), col.data(), val.data(), pb.data(), nblocks, &H, &berr) !=
+        EKCG_OK) {
+        set_error("ekcg_set_block_jacobi", berr.c_str());
+        return EKCG_EINVAL;
+    }
+    auto& lrp = H.lrp;
+    auto& lci = H.lci;
+    auto& lv = H.lv;
+    auto& diag = H.diag;
+    auto& urp = H.urp;
+    auto& uci = H.uci;
+    auto& uv = H.uv;
+    auto& fblk = H.fblk;
+    auto& flv = H.flv;
+    auto& frows = H.frows;
+    auto& bblk = H.bblk;
+    auto& blv = H.blv;
+    auto& brows = H.brows;
+    auto up = [&](auto** dst, const auto& src) -> int {
+        using E = typename std::remove_reference<decltype(src[0])>::type;
+        const size_t bytes = std::max<size_t>(1, src.size()) * sizeof(E);
+        if (cudaMalloc((void**)dst, bytes) != cudaSuccess) return EKCG_ENOMEM;
+        if (!src.empty() && cudaMemcpy(*dst, src.data(), src.size() * sizeof(E),
+                                       cudaMemcpyHostToDevice) != cudaSuccess)
+            return EKCG_ECUDA;
+        return EKCG_OK;
+    };
+    int rc = EKCG_OK;
+    if (rc == EKCG_OK) rc = up(&c->bj_frp, lrp);
+    if (rc == EKCG_OK) rc = up(&c->bj_fci, lci);
+    if (rc == EKCG_OK) rc = up(&c->bj_fv, lv);
+    if (rc == EKCG_OK) rc = up(&c->bj_fblk, fblk);
+    if (rc == EKCG_OK) rc = up(&c->bj_flev, flv);
+    if (rc == EKCG_OK) rc = up(&c->bj_frows, frows);
+    if (rc == EKCG_OK) rc = up(&c->bj_brp, urp);
+    if (rc == EKCG_OK) rc = up(&c->bj_bci, uci);
+    if (rc == EKCG_OK) rc = up(&c->bj_bv, uv);
+    if (rc == EKCG_OK) rc = up(&c->bj_bblk, bblk);
+    if (rc == EKCG_OK) rc = up(&c->bj_blev, blv);
+    if (rc == EKCG_OK) rc = up(&c->bj_brows, brows);
+    if (rc == EKCG_OK) rc = up(&c->bj_diag, diag);
+    if (rc == EKCG_OK && cudaMalloc(&c->bj_vec, n * sizeof(double)) != cudaSuccess)
+        rc = EKCG_ENOMEM;
+    if (rc != EKCG_OK) {
+        free_block_jacobi(c);
+        set_error("ekcg_set_block_jacobi", "device memory");
+        return rc;
+    }
+    c->bj_nblk = nblocks;
+    return EKCG_OK;
+}
+
+int ekcg_block_ic0_host(int64_t n, const int64_t* rowptr, const int32_t* colind,
+                        const double* val, const int32_t* bpart, int nblocks, double* lval,
+                        int32_t* fwd_level, int32_t* bwd_level) {
+    if (n < 1 || !rowptr || !colind || !val || !bpart || nblocks < 1 || !lval || !fwd_level ||
+        !bwd_level || rowptr[0] != 0 || rowptr[n] > INT32_MAX)
+        return EKCG_EINVAL;
+    std::vector<int32_t> rp(n + 1);
+    for (int64_t i = 0; i <= n; ++i) rp[i] = (int32_t)rowptr[i];
+    for (int64_t i = 0; i < n; ++i) {
+        if (bpart[i] < 0 || bpart[i] >= nblocks) return EKCG_EINVAL;
+        for (int32_t e = rp[i]; e < rp[i + 1]; ++e)
+            if (colind[e] < 0 || colind[e] >= n || (e > rp[i] && colind[e - 1] >= colind[e]))
+                return EKCG_EINVAL;
+    }
+    BJHost H;
+    std::string err;
+    const int rc = bj_build_host(n, rp.data(), colind, val, bpart, nblocks, &H, &err);
+    if (rc != EKCG_OK) {
+        set_error("ekcg_block_ic0_host", err.c_str());
+        return rc;
+    }
+    for (int64_t i = 0; i < n; ++i) {
+        int32_t a = H.lrp[i];
+        for (int32_t e = rp[i]; e < rp[i + 1]; ++e) {
+            const int32_t k = colind[e];
+            if (k == i)
+                lval[e] = H.diag[i];
+            else if (a < H.lrp[i + 1] && H.lci[a] == k)
+                lval[e] = H.lv[a++];
+            else
+                lval[e] = 0.0;
+        }
+        fwd_level[i] = H.flev[i];
+        bwd_level[i] = H.blev[i];
+    }
     return EKCG_OK;
 }
 

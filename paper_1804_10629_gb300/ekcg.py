@@ -67,6 +67,11 @@ def _declare(L):
     L.ekcg_get_perm.restype = c_int
     L.ekcg_last_stats.argtypes = [c_void_p, POINTER(c_int64), POINTER(c_int64)]
     L.ekcg_last_stats.restype = c_int
+    L.ekcg_block_ic0_host.argtypes = [c_int64, c_void_p, c_void_p, c_void_p, c_void_p, c_int,
+                                      c_void_p, c_void_p, c_void_p]
+    L.ekcg_block_ic0_host.restype = c_int
+    L.ekcg_set_block_jacobi.argtypes = [c_void_p, c_void_p, c_int]
+    L.ekcg_set_block_jacobi.restype = c_int
     L.ekcg_wait_selftest.argtypes = [c_longlong, c_void_p]
     L.ekcg_wait_selftest.restype = c_int
     L.ekcg_set_profile.argtypes = [c_void_p, c_int]
@@ -217,6 +222,23 @@ def ekcg_last_stats(ctx):
     return kl.value, sp.value
 
 
+def ekcg_block_ic0_host(A, bpart):
+    """(lval, fwd_level, bwd_level) of the host preconditioner setup for a CSR matrix A
+    (rows in their given order) and block ids bpart (host computation only)."""
+    rp = np.ascontiguousarray(A.rowptr, dtype=np.int64)
+    ci = np.ascontiguousarray(A.colind, dtype=np.int32)
+    va = np.ascontiguousarray(A.val, dtype=np.float64)
+    bp = np.ascontiguousarray(bpart, dtype=np.int32)
+    lval = np.zeros(len(va))
+    fl = np.zeros(A.n, dtype=np.int32)
+    bl = np.zeros(A.n, dtype=np.int32)
+    st = lib().ekcg_block_ic0_host(A.n, _ptr(rp), _ptr(ci), _ptr(va), _ptr(bp),
+                                   int(bp.max()) + 1, _ptr(lval), _ptr(fl), _ptr(bl))
+    if st != EKCG_OK:
+        raise EkcgError(st, "ekcg_block_ic0_host")
+    return lval, fl, bl
+
+
 def ekcg_wait_selftest(limit_cycles, stream=None):
     """Status of the bounded-wait diagnostic (EKCG_ETIMEOUT when the wait ran out)."""
     return lib().ekcg_wait_selftest(int(limit_cycles), c_void_p(stream))
@@ -346,6 +368,17 @@ class Solver:
 
     def profile(self):
         return ekcg_profile(self.ctx)
+
+    def set_block_jacobi(self, bpart):
+        """Block Jacobi IC(0) preconditioner over the blocks of bpart (natural row order);
+        None removes it."""
+        if bpart is None:
+            st = lib().ekcg_set_block_jacobi(self.ctx, None, 0)
+        else:
+            bp = np.ascontiguousarray(bpart, dtype=np.int32)
+            st = lib().ekcg_set_block_jacobi(self.ctx, _ptr(bp), int(bp.max()) + 1)
+        if st != EKCG_OK:
+            raise EkcgError(st, "ekcg_set_block_jacobi")
 
     def set_profile(self, on):
         """Per-launch CUDA-event timing of later solves on or off."""

@@ -160,6 +160,45 @@ def test_restructured_msdo_is_rejected():
 
 
 @pytest.mark.parametrize("variant", ["sre", "sre2", "msdo"])
+@pytest.mark.parametrize("s", [1, 2])
+def test_block_jacobi_parity(variant, s):
+    """Split preconditioned s-step forms (Algorithms 8-10) with block Jacobi IC(0) over 16
+    boxes inside the 4 domains, against the oracle (its own IC(0) and triangular solves)."""
+    A, b, part = ragged_problem()
+    bpart = wl.partition_boxes((45, 37), 16)
+    M = o.BlockJacobi(A, bpart, "ic0")
+    ref = o.solve(A, b, part, 4, s, tol=1e-8, maxit=2000, variant=variant, precond=M)
+    S = ekcg.Solver(A, 4, part, variant=variant, max_s=s, max_basis_bytes=8 << 30)
+    S.set_block_jacobi(bpart)
+    x, it, hist, st = S.solve(dev(b), s=s, tol=1e-8, maxit=2000)
+    x = x.cpu().numpy()
+    S.close()
+    assert st == ref.status == o.OK, (st, ref.status)
+    assert abs(it - ref.iters) <= 1, (it, ref.iters)
+    m = min(21, len(hist), len(ref.hist))
+    np.testing.assert_allclose(hist[:m], np.array(ref.hist[:m]), rtol=1e-6, atol=0)
+    assert relres(A, b, x) <= 1e-8 * 1.01
+    assert np.linalg.norm(x - ref.x) <= 1e-8 * np.linalg.norm(ref.x)
+
+
+def test_block_jacobi_rejections():
+    A, b, part = ragged_problem()
+    S = ekcg.Solver(A, 4, part, max_s=2)
+    with pytest.raises(ekcg.EkcgError):        # blocks across the 4 domains
+        S.set_block_jacobi(wl.partition_strips(A.n, 3))
+    S.set_block_jacobi(wl.partition_boxes((45, 37), 16))
+    S.set_block_jacobi(None)                   # removed: the plain solve again
+    x, it, hist, st = S.solve(dev(b), s=2, tol=1e-8, maxit=2000)
+    ref = o.solve(A, b, part, 4, 2, tol=1e-8, maxit=2000)
+    assert st == 0 and abs(it - ref.iters) <= 1
+    S.close()
+    F = ekcg.Solver(A, 4, part, precision="fp32_ir", max_s=2)
+    with pytest.raises(ekcg.EkcgError):
+        F.set_block_jacobi(wl.partition_boxes((45, 37), 16))
+    F.close()
+
+
+@pytest.mark.parametrize("variant", ["sre", "sre2", "msdo"])
 def test_precholqr_parity(variant):
     A, b, part = ragged_problem(t=8)
     check_parity(A, b, part, 8, 2, variant, "sstep", "precholqr")
