@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--variant", default="")
     ap.add_argument("--basis", default="sstep")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32_ir"])
+    ap.add_argument("--precond", default=None, choices=["ic0"],
+                    help="block Jacobi split preconditioning, IC(0) blocks on 64 boxes")
     ap.add_argument("--sweep", action="store_true",
                     help="stability sweep over s in {1,2,4,8} and both precisions")
     ap.add_argument("--tol", type=float, default=1e-8)
@@ -507,6 +509,10 @@ def main():
         S = ekcg.Solver(prob.A, prob.t, prob.part, variant=variant, basis=args.basis,
                         precision=args.precision, max_s=s, profile=True,
                         stream=stream.cuda_stream, max_basis_bytes=64 << 30)
+    if args.precond:
+        # block Jacobi over 64 geometric boxes (the paper's 64 subdomains), each inside one
+        # of the workload's t domains
+        S.set_block_jacobi(wl.partition_boxes(prob.shape, 64))
     setup_s = time.perf_counter() - t0
     b = torch.as_tensor(prob.b, dtype=torch.float64, device="cuda")
     x = torch.empty_like(b)
@@ -521,7 +527,7 @@ def main():
 
     # the same workload through the float32 inner solve with float64 refinement
     mixed = None
-    if args.precision == "fp64" and not args.no_mixed:
+    if args.precision == "fp64" and not args.no_mixed and not args.precond:
         with torch.cuda.stream(stream):
             M = ekcg.Solver(prob.A, prob.t, prob.part, variant=variant, basis=args.basis,
                             precision="fp32_ir", max_s=s, profile=True,
@@ -583,6 +589,8 @@ def main():
                        "true_relres": relres, "status": st,
                        "l2": "working set larger than L2 (matrix + n x t blocks)",
                        "setup_s": setup_s, "parallelism": "replicas",
+                       "precond": ("block Jacobi, IC(0) blocks on 64 boxes" if args.precond
+                                   else None),
                        "profiling": "timed solves without per-launch events; kernel table from one more solve with CUDA events around every launch"},
             "roofline": roof, "kernels": kernel_table, "gpu_launches": launches,
             "mixed": mixed,
