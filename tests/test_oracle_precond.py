@@ -321,3 +321,18 @@ def test_pcg_beta_without_preconditioner_is_caught(monkeypatch):
         return res
     monkeypatch.setattr(o, "pcg", bad)
     assert not _precond_pins_hold()
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("variant", ["sre", "sre2", "msdo"])
+def test_preconditioned_ca7_matches_sstep_counts(variant):
+    """Section 5 (Table 5): with block Jacobi IC(0) preconditioning, the s-step versions and
+    their CA versions with Algorithm 7 converge in (nearly) the same number of iterations on
+    Poisson2D; the printed t = 4 rows differ by at most one."""
+    A, b, M = _paper_setup("ic0")
+    part = wl.partition_boxes((100, 100), 4)
+    for s in (2, 4, 8):
+        ks = o.solve(A, b, part, 4, s, tol=1e-6, maxit=1000, variant=variant, precond=M).iters
+        kc = o.solve(A, b, part, 4, s, tol=1e-6, maxit=1000, variant=variant, basis="ca7",
+                     precond=M).iters
+        assert abs(ks - kc) <= 1, (variant, s, ks, kc)
