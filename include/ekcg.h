@@ -61,6 +61,17 @@ extern "C" {
 #define EKCG_FP64 0       /* all vectors and arithmetic in float64                       */
 #define EKCG_FP32_IR 1    /* float32 inner solve in a float64 iterative-refinement loop   */
 
+/* Arithmetic of the float64 tall-skinny contractions (CGS update W - Q C):               */
+#define EKCG_CONTRACT_FP64 0   /* float64 fused multiply-adds                             */
+#define EKCG_CONTRACT_SPLIT 1  /* float64-accurate split products on the bf16 tensor cores:
+                                * eight 7-bit slices per value (56-bit fixed point against
+                                * the row / column binade), the 36 slice pairs with
+                                * a + b <= 9 summed exactly in fp32 tensor memory, groups
+                                * combined in 64-bit integers; error per term about 2^-52 of
+                                * max|row| max|column|.  Shapes it does not take (more than
+                                * 64 contracted columns per launch, widths other than 16 or
+                                * 32) use float64 FMAs.                                     */
+
 typedef struct ekcg_ctx ekcg_ctx;
 
 typedef struct {
@@ -76,10 +87,12 @@ typedef struct {
     double inner_tol;     /* FP32_IR: relative residual reduction of each inner solve      */
     int max_refine;       /* FP32_IR: maximum outer refinement steps                       */
     int profile;          /* 1: time every kernel class with CUDA events (ekcg_profile)   */
+    int contraction;      /* EKCG_CONTRACT_FP64 / EKCG_CONTRACT_SPLIT (float64 path)      */
 } ekcg_opts;
 
 /* Fill *opts with the defaults: SRE, SSTEP, ACHOLQR, FP64, max_s 8, max_blocks 0,
- * max_basis_bytes 0, breakdown_tol 1e-14, inner_tol 1e-4, max_refine 30, profile 0.      */
+ * max_basis_bytes 0, breakdown_tol 1e-14, inner_tol 1e-4, max_refine 30, profile 0,
+ * contraction EKCG_CONTRACT_FP64.                                                         */
 void ekcg_default_opts(ekcg_opts* opts);
 
 /* Build a solver context for the SPD matrix A (Section 2) and its t-way partition.
@@ -192,6 +205,23 @@ int ekcg_split_T(ekcg_ctx* ctx, const double* r, double* T);
  * for max_s*t columns).  Two-stage deterministic reduction through the context's
  * workspace.                                                                             */
 int ekcg_gram(ekcg_ctx* ctx, const double* X, int p, const double* Y, int q, double* C);
+
+/* OUT = Y - X C, the CGS update of Section 3.1 (W <- W - Q C): X n x p, Y and OUT n x q,
+ * C p x q, all row-major device doubles (OUT may be Y; X must not overlap OUT).
+ * contraction: EKCG_CONTRACT_FP64 (float64 FMAs, any 1 <= p <= 256, 1 <= q <= 256) or
+ * EKCG_CONTRACT_SPLIT (tensor-core split products; p a multiple of 16 up to 64 and
+ * q = 16 or 32, 16-byte aligned buffers; other shapes return EKCG_EINVAL).  Enqueued on
+ * the context's stream; returns EKCG_ETIMEOUT if a bounded device wait ran out.           */
+int ekcg_sub_xc(ekcg_ctx* ctx, const double* X, int p, const double* C, const double* Y,
+                int q, double* OUT, int contraction);
+
+/* ekcg_gram with an explicit contraction: EKCG_CONTRACT_FP64 (any 1 <= p, q <= 256) or
+ * EKCG_CONTRACT_SPLIT (tensor-core split products over tiles of 128 rows, each column
+ * scaled by its binade over the tile; p a multiple of 16 up to 64 and q = 16 or 32, other
+ * shapes return EKCG_EINVAL).  Synchronises the context's stream; EKCG_ETIMEOUT if a
+ * bounded device wait ran out.                                                           */
+int ekcg_gram_with(ekcg_ctx* ctx, const double* X, int p, const double* Y, int q, double* C,
+                   int contraction);
 
 /* Allocation-free C = X^T Y.  The paper has no counterpart: this serves callers that cannot
  * allocate device memory, such as code running while a stream is captured into a CUDA graph

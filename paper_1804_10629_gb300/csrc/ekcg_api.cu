@@ -18,6 +18,7 @@
 #include "kernels.cuh"
 #include "bulk.cuh"
 #include "precond.cuh"
+#include "ozaki.cuh"
 
 using namespace ekcg;
 
@@ -46,13 +47,13 @@ void set_error(const char* where, const char* what) {
 
 enum KClass {
     KC_SPMM = 0, KC_GRAM, KC_REDUCE, KC_UPDATE, KC_CHOL, KC_XR, KC_RESID, KC_SPLIT, KC_PERM,
-    KC_COPY, KC_NORM, KC_MISC, KC_GRAM_DF, KC_PRECOND, KC_COUNT
+    KC_COPY, KC_NORM, KC_MISC, KC_GRAM_DF, KC_PRECOND, KC_TRSM, KC_COUNT
 };
 // gram_df: the float-float upper-triangle Gram of the float32 path (FP32-pipe bound; its
 // operation count is 10 FP32 operations per multiply-add)
 const char* kClassNames[KC_COUNT] = {"spmm", "gram", "gram_reduce", "block_update", "chol_inv",
                                      "xr_update", "residual", "split_T", "permute", "copy",
-                                     "norm", "misc", "gram_df", "precond"};
+                                     "norm", "misc", "gram_df", "precond", "trsm"};
 
 }  // namespace
 
@@ -354,10 +355,54 @@ template <typename T, typename Acc>
 bool gram_fast_path(ekcg_ctx* c, MB<const T> X, MB<const T> Y, Acc* partials, int* g, int* rc) {
     return false;
 }
+// float64 C = X^T Y on the tensor cores (ozaki.cuh): one CTA per SM, each writing its
+// partial sum in the k_gram_reduce layout (tile 0, entry p * Q + q).
+template <int P, int Q>
+int launch_oz_gram(ekcg_ctx* c, MB<const double> X, MB<const double> Y, double* partials,
+                   int* g) {
+    using S = oz::GramShape<P, Q>;
+    static bool attr = false;
+    if (!attr) {
+        EK_CUDA(cudaFuncSetAttribute(oz::k_oz_gram<P, Q>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, S::kSmem));
+        attr = true;
+    }
+    const int64_t ntile = (c->n + oz::kGramRows - 1) / oz::kGramRows;
+    *g = (int)std::max<int64_t>(1, std::min<int64_t>(ntile, (int64_t)c->num_sms));
+    {
+        Launch L(c, KC_GRAM, 2.0 * (double)c->n * P * Q, (double)c->n * (P + Q) * sizeof(double));
+        oz::k_oz_gram<P, Q><<<*g, oz::kGramThreads, S::kSmem, c->stream>>>(X, Y, c->n, partials,
+                                                                          c->flag);
+    }
+    return EKCG_OK;
+}
+
+bool oz_gram_shape(const ekcg_ctx* c, MB<const double> X, MB<const double> Y) {
+    const int P = X.cols(), Q = Y.cols();
+    return c->opts.contraction == EKCG_CONTRACT_SPLIT && (Q == 16 || Q == 32) && P % 16 == 0 &&
+           P >= 16 && P <= 64 && X.w % 8 == 0 && Y.count == 1 && Y.w == Q;
+}
+
 template <>
 bool gram_fast_path<double, double>(ekcg_ctx* c, MB<const double> X, MB<const double> Y,
                                     double* partials, int* g, int* rc) {
     const int P = X.cols(), Q = Y.cols();
+    if (oz_gram_shape(c, X, Y)) {
+        if (Q == 32) {
+            switch (P) {
+                case 16: *rc = launch_oz_gram<16, 32>(c, X, Y, partials, g); return true;
+                case 32: *rc = launch_oz_gram<32, 32>(c, X, Y, partials, g); return true;
+                case 48: *rc = launch_oz_gram<48, 32>(c, X, Y, partials, g); return true;
+                default: *rc = launch_oz_gram<64, 32>(c, X, Y, partials, g); return true;
+            }
+        }
+        switch (P) {
+            case 16: *rc = launch_oz_gram<16, 16>(c, X, Y, partials, g); return true;
+            case 32: *rc = launch_oz_gram<32, 16>(c, X, Y, partials, g); return true;
+            case 48: *rc = launch_oz_gram<48, 16>(c, X, Y, partials, g); return true;
+            default: *rc = launch_oz_gram<64, 16>(c, X, Y, partials, g); return true;
+        }
+    }
     auto al = [](const MB<const double>& m) {
         return (m.stride % 2) == 0 && ((uintptr_t)m.base % 16) == 0;
     };
@@ -467,7 +512,11 @@ int run_gram_chunk(ekcg_ctx* c, MB<const T> X, MB<const T> Y, Out* C, int ldc, i
 template <typename T, typename Acc, typename Out>
 int run_gram(ekcg_ctx* c, MB<const T> X, MB<const T> Y, Out* C, Acc* partials) {
     const int Q = Y.cols();
-    const int per = std::max(1, kPMax / X.w);
+    // the split-product Gram contracts at most 64 columns of X per launch
+    const bool split = std::is_same<T, double>::value &&
+                       c->opts.contraction == EKCG_CONTRACT_SPLIT && (Q == 16 || Q == 32) &&
+                       X.w % 16 == 0 && X.w <= 64;
+    const int per = std::max(1, (split ? 64 : kPMax) / X.w);
     for (int b0 = 0; b0 < X.count; b0 += per) {
         MB<const T> Xc = X;
         Xc.first = (X.first + b0) % X.ring;
@@ -483,6 +532,8 @@ int run_gram(ekcg_ctx* c, MB<const T> X, MB<const T> Y, Out* C, Acc* partials) {
 template <typename T>
 int run_gram_upper(ekcg_ctx* c, MB<const T> X, MB<const T> Y, double* C) {
     const int M = X.cols();
+    if (std::is_same<T, double>::value && c->opts.contraction == EKCG_CONTRACT_SPLIT)
+        return run_gram<T, double, double>(c, X, Y, C, c->partials);   // full, split products
     const bool fits = X.count == 1 && Y.count == 1 && X.w == Y.w && (M == 16 || M == 32) &&
                       ((uintptr_t)X.blk(0) % 16) == 0 && ((uintptr_t)Y.blk(0) % 16) == 0;
     if (fits)
@@ -528,6 +579,74 @@ template <typename T, typename CT>
 bool update_fast_path(ekcg_ctx* c, MB<const T> X, const CT* C, int ldc, int c_row0,
                       MB<const T> Y, MB<T> OUT, int beta_on, CT alpha, int upper, int* rc) {
     return false;
+}
+
+// float64 CGS update OUT = Y - X C on the tensor cores (ozaki.cuh): grid = resident CTAs,
+// limited by shared memory and by the 512 tensor-memory columns of an SM.
+template <int P, int Q>
+int launch_oz_update(ekcg_ctx* c, MB<const double> X, const double* C, MB<const double> Y,
+                     MB<double> OUT, int beta_on) {
+    using S = oz::UpdShape<P, Q>;
+    static bool attr = false;
+    if (!attr) {
+        EK_CUDA(cudaFuncSetAttribute(oz::k_oz_update<P, Q>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, S::kSmem));
+        attr = true;
+    }
+    const int64_t ntile = (c->n + oz::kTile - 1) / oz::kTile;
+    const int g = (int)std::min<int64_t>(ntile, (int64_t)c->num_sms);
+    oz::k_oz_update<P, Q><<<g, oz::kUpdThreads, S::kSmem, c->stream>>>(
+        X, C, Y, OUT, c->n, beta_on, c->flag);
+    return EKCG_OK;
+}
+
+// Shapes the split-product update takes: the CGS step (beta 1, alpha -1) or the product
+// with R^{-1} in place (beta 0, alpha 1, X = OUT), C with ldc = Q, P = 16..64 contracted
+// columns in blocks of a multiple of 8, Q = 16 or 32, single-block Y and OUT; X overlaps
+// OUT only as the in-place product.
+bool oz_update_shape(const ekcg_ctx* c, MB<const double> X, int ldc, MB<const double> Y,
+                     MB<double> OUT, int beta_on, double alpha, int upper) {
+    const int P = X.cols(), Q = OUT.cols();
+    if (c->opts.contraction != EKCG_CONTRACT_SPLIT) return false;
+    if (ldc != Q) return false;
+    if (!(Q == 16 || Q == 32) || P % 16 || P < 16 || P > 64 || X.w % 8) return false;
+    if (OUT.count != 1 || OUT.w != Q) return false;
+    if (beta_on) {
+        if (alpha != -1.0 || upper || Y.count != 1 || Y.w != Q) return false;
+        for (int a = 0; a < X.count; ++a) {
+            const double* xb = X.blk(a);
+            const double* ob = OUT.blk(0);
+            if (xb < ob + c->n * (int64_t)Q && ob < xb + c->n * (int64_t)X.w) return false;
+        }
+        return true;
+    }
+    // in place: X is exactly OUT
+    return alpha == 1.0 && X.count == 1 && X.w == Q && X.blk(0) == (const double*)OUT.blk(0);
+}
+
+template <>
+bool update_fast_path<double, double>(ekcg_ctx* c, MB<const double> X, const double* C,
+                                      int ldc, int c_row0, MB<const double> Y,
+                                      MB<double> OUT, int beta_on, double alpha, int upper,
+                                      int* rc) {
+    if (!oz_update_shape(c, X, ldc, Y, OUT, beta_on, alpha, upper)) return false;
+    const double* Cp = C + (int64_t)c_row0 * ldc;
+    const int P = X.cols(), Q = OUT.cols();
+    const MB<const double> Yc = Y;
+    if (Q == 32) {
+        switch (P) {
+            case 16: *rc = launch_oz_update<16, 32>(c, X, Cp, Yc, OUT, beta_on); return true;
+            case 32: *rc = launch_oz_update<32, 32>(c, X, Cp, Yc, OUT, beta_on); return true;
+            case 48: *rc = launch_oz_update<48, 32>(c, X, Cp, Yc, OUT, beta_on); return true;
+            default: *rc = launch_oz_update<64, 32>(c, X, Cp, Yc, OUT, beta_on); return true;
+        }
+    }
+    switch (P) {
+        case 16: *rc = launch_oz_update<16, 16>(c, X, Cp, Yc, OUT, beta_on); return true;
+        case 32: *rc = launch_oz_update<32, 16>(c, X, Cp, Yc, OUT, beta_on); return true;
+        case 48: *rc = launch_oz_update<48, 16>(c, X, Cp, Yc, OUT, beta_on); return true;
+        default: *rc = launch_oz_update<64, 16>(c, X, Cp, Yc, OUT, beta_on); return true;
+    }
 }
 template <>
 bool update_fast_path<float, float>(ekcg_ctx* c, MB<const float> X, const float* C, int ldc,
@@ -624,7 +743,11 @@ int run_update_chunk(ekcg_ctx* c, MB<const T> X, const CT* C, int ldc, int c_row
 // OUT = Y - X C  (C is X.cols() x OUT.cols(), ldc = OUT.cols()); X chunked by kPMax columns.
 template <typename T, typename CT>
 int run_sub(ekcg_ctx* c, MB<const T> X, const CT* C, MB<const T> Y, MB<T> OUT) {
-    const int per = std::max(1, kPMax / X.w);
+    // the split-product update contracts at most 64 columns per launch
+    const bool split = std::is_same<T, double>::value &&
+                       c->opts.contraction == EKCG_CONTRACT_SPLIT && X.w % 16 == 0 &&
+                       X.w <= 64;
+    const int per = std::max(1, (split ? 64 : kPMax) / X.w);
     const int Q = OUT.cols();
     for (int b0 = 0; b0 < X.count; b0 += per) {
         MB<const T> Xc = X;
@@ -641,6 +764,28 @@ template <typename T, typename CT>
 int run_rmul(ekcg_ctx* c, MB<T> X, const CT* Rinv) {
     return run_update_chunk<T, CT>(c, as_const(X), Rinv, X.cols(), 0, as_const(X), X, 0, CT(1),
                                    1);
+}
+
+// X <- X R^{-1} in place by row-wise forward substitution (float64 basis; see k_trsm_rows).
+int run_trsm(ekcg_ctx* c, MB<double> X) {
+    const int m = X.cols();
+    int rows = 128;
+    while (rows > 32 && (size_t)rows * (m | 1) * sizeof(double) > 96 * 1024) rows >>= 1;
+    const size_t smem = (size_t)rows * (m | 1) * sizeof(double);
+    static bool attr = false;
+    if (!attr) {
+        EK_CUDA(cudaFuncSetAttribute(k_trsm_rows<double>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024));
+        attr = true;
+    }
+    const int64_t tiles = (c->n + rows - 1) / rows;
+    const int g = (int)std::min<int64_t>(tiles, (int64_t)c->num_sms * 8);
+    {
+        const double nn = (double)c->n;
+        Launch L(c, KC_TRSM, nn * (double)m * m, 2.0 * nn * m * sizeof(double));
+        k_trsm_rows<double><<<g, rows, smem, c->stream>>>(X, c->R, c->Rinv, m, c->n);
+    }
+    return check_launch("k_trsm_rows");
 }
 
 int run_chol(ekcg_ctx* c, int m) {
@@ -664,7 +809,6 @@ __global__ void k_d2f(float* __restrict__ y, const double* __restrict__ x, int m
 }
 
 template <typename T> const T* rinv_for(ekcg_ctx* c, int m);
-template <> const double* rinv_for<double>(ekcg_ctx* c, int) { return c->Rinv; }
 template <> const float* rinv_for<float>(ekcg_ctx* c, int m) {
     k_d2f<<<std::max(1, std::min((m * m + 255) / 256, 1024)), 256, 0, c->stream>>>(c->Rinv32,
                                                                                    c->Rinv, m * m);
@@ -749,6 +893,25 @@ struct Engine {
         return EKCG_OK;
     }
 
+    // W <- W R^{-1} and A W <- (A W) R^{-1} with the factor of the last run_chol: in float64
+    // row-wise triangular solves (as the oracle's), or with the split contraction on single
+    // blocks of width 16 / 32 the tensor-core product with the inverted factor; in float32
+    // the product with R^{-1}.
+    int apply_rinv(int64_t j, int cnt) {
+        if constexpr (std::is_same<T, double>::value) {
+            if (c->opts.contraction == EKCG_CONTRACT_SPLIT && cnt == 1 && (t == 16 || t == 32)) {
+                EK_TRY((run_rmul<T, T>(c, Wm(j, cnt), c->Rinv)));
+                return run_rmul<T, T>(c, Zm(j, cnt), c->Rinv);
+            }
+            EK_TRY(run_trsm(c, Wm(j, cnt)));
+            return run_trsm(c, Zm(j, cnt));
+        } else {
+            const T* Ri = rinv_for<T>(c, cnt * t);
+            EK_TRY((run_rmul<T, T>(c, Wm(j, cnt), Ri)));
+            return run_rmul<T, T>(c, Zm(j, cnt), Ri);
+        }
+    }
+
     // A-CholQR (or Pre-CholQR) of blocks [j, j+cnt) viewed as one n x (cnt t) matrix, with
     // Z = A W on entry; A W is carried through the triangular factors.
     int self_orth(int64_t j, int cnt) {
@@ -758,17 +921,12 @@ struct Engine {
             for (int rep = 0; rep < 2; ++rep) {
                 EK_TRY(run_gram_upper<T>(c, as_const(Wm(j, cnt)), as_const(Wm(j, cnt)), c->G));
                 EK_TRY(run_chol(c, m));
-                const T* Ri = rinv_for<T>(c, m);
-                EK_TRY((run_rmul<T, T>(c, Wm(j, cnt), Ri)));
-                EK_TRY((run_rmul<T, T>(c, Zm(j, cnt), Ri)));
+                EK_TRY(apply_rinv(j, cnt));
             }
         }
         EK_TRY(run_gram_upper<T>(c, as_const(Wm(j, cnt)), as_const(Zm(j, cnt)), c->G));
         EK_TRY(run_chol(c, m));
-        const T* Ri = rinv_for<T>(c, m);
-        EK_TRY((run_rmul<T, T>(c, Wm(j, cnt), Ri)));
-        EK_TRY((run_rmul<T, T>(c, Zm(j, cnt), Ri)));
-        return EKCG_OK;
+        return apply_rinv(j, cnt);
     }
 
     // Q window for block j (SRE: W_{j-2}, W_{j-1} that exist; full: all previous).
@@ -1517,6 +1675,7 @@ void ekcg_default_opts(ekcg_opts* o) {
     o->inner_tol = 1e-4;
     o->max_refine = 30;
     o->profile = 0;
+    o->contraction = EKCG_CONTRACT_FP64;
 }
 
 int ekcg_setup(int64_t n, const int64_t* rowptr, const int32_t* colind, const double* val,
@@ -1537,7 +1696,8 @@ int ekcg_setup(int64_t n, const int64_t* rowptr, const int32_t* colind, const do
         (o.basis == EKCG_RESTRUCT && o.variant == EKCG_MSDO) || o.orth < 0 ||
         o.orth > 1 || o.precision < 0 || o.precision > 1 || o.max_s < 1 ||
         o.max_s * t > kPMax || o.max_blocks < 0 || !(o.breakdown_tol >= 0) ||
-        !(o.inner_tol > 0 && o.inner_tol < 1) || o.max_refine < 1) {
+        !(o.inner_tol > 0 && o.inner_tol < 1) || o.max_refine < 1 ||
+        (o.contraction != EKCG_CONTRACT_FP64 && o.contraction != EKCG_CONTRACT_SPLIT)) {
         set_error("ekcg_setup", "invalid options (note: max_s * t must be <= 256)");
         delete c;
         return EKCG_EINVAL;
@@ -1831,6 +1991,69 @@ int ekcg_gram(ekcg_ctx* c, const double* X, int p, const double* Y, int q, doubl
     MB<const double> Ym = mb<const double>(Y, 0, 0, 1, 1, q);
     EK_TRY((run_gram_chunk<double, double, double>(c, Xm, Ym, C, q, 0, c->partials)));
     EK_CUDA(cudaStreamSynchronize(c->stream));
+    return EKCG_OK;
+}
+
+int ekcg_sub_xc(ekcg_ctx* c, const double* X, int p, const double* C, const double* Y, int q,
+                double* OUT, int contraction) {
+    if (!c || !X || !C || !Y || !OUT || p < 1 || q < 1 || p > kPMax || q > kPMax ||
+        (contraction != EKCG_CONTRACT_FP64 && contraction != EKCG_CONTRACT_SPLIT)) {
+        set_error("ekcg_sub_xc", "bad arguments");
+        return EKCG_EINVAL;
+    }
+    MB<const double> Xm = mb<const double>(X, 0, 0, 1, 1, p);
+    MB<const double> Ym = mb<const double>(Y, 0, 0, 1, 1, q);
+    MB<double> Om = mb<double>(OUT, 0, 0, 1, 1, q);
+    const int saved = c->opts.contraction;
+    c->opts.contraction = contraction;
+    if (contraction == EKCG_CONTRACT_SPLIT &&
+        (!oz_update_shape(c, Xm, q, Ym, Om, 1, -1.0, 0) || ((uintptr_t)X % 16) ||
+         ((uintptr_t)Y % 16) || ((uintptr_t)OUT % 16))) {
+        c->opts.contraction = saved;
+        set_error("ekcg_sub_xc", "split products take p = 16, 32, 48, 64 and q = 16, 32");
+        return EKCG_EINVAL;
+    }
+    EK_CUDA(cudaMemsetAsync(c->flag, 0, sizeof(int), c->stream));
+    const int rc = run_sub<double, double>(c, Xm, C, Ym, Om);
+    c->opts.contraction = saved;
+    EK_TRY(rc);
+    int flag = 0;
+    EK_CUDA(cudaMemcpyAsync(&flag, c->flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    EK_CUDA(cudaStreamSynchronize(c->stream));
+    if (flag & 4) {
+        set_error("ekcg_sub_xc", "a bounded device wait ran out");
+        return EKCG_ETIMEOUT;
+    }
+    return EKCG_OK;
+}
+
+int ekcg_gram_with(ekcg_ctx* c, const double* X, int p, const double* Y, int q, double* C,
+                   int contraction) {
+    if (!c || !X || !Y || !C || p < 1 || q < 1 || p > kPMax || q > kPMax ||
+        (contraction != EKCG_CONTRACT_FP64 && contraction != EKCG_CONTRACT_SPLIT)) {
+        set_error("ekcg_gram_with", "bad arguments");
+        return EKCG_EINVAL;
+    }
+    MB<const double> Xm = mb<const double>(X, 0, 0, 1, 1, p);
+    MB<const double> Ym = mb<const double>(Y, 0, 0, 1, 1, q);
+    const int saved = c->opts.contraction;
+    c->opts.contraction = contraction;
+    if (contraction == EKCG_CONTRACT_SPLIT && !oz_gram_shape(c, Xm, Ym)) {
+        c->opts.contraction = saved;
+        set_error("ekcg_gram_with", "split products take p = 16, 32, 48, 64 and q = 16, 32");
+        return EKCG_EINVAL;
+    }
+    EK_CUDA(cudaMemsetAsync(c->flag, 0, sizeof(int), c->stream));
+    const int rc = run_gram_chunk<double, double, double>(c, Xm, Ym, C, q, 0, c->partials);
+    c->opts.contraction = saved;
+    EK_TRY(rc);
+    int flag = 0;
+    EK_CUDA(cudaMemcpyAsync(&flag, c->flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    EK_CUDA(cudaStreamSynchronize(c->stream));
+    if (flag & 4) {
+        set_error("ekcg_gram_with", "a bounded device wait ran out");
+        return EKCG_ETIMEOUT;
+    }
     return EKCG_OK;
 }
 

@@ -734,6 +734,51 @@ __global__ void k_chol_inv(const double* __restrict__ G, int m, double* __restri
 }
 
 // ---------------------------------------------------------------------------------------
+// X <- X R^{-1} by forward substitution along every row (A-CholQR, Section 3.1): each row
+// x of the result solves x R = w for the row w of X, R upper triangular.  Right-looking
+// order: x_i = w_i * (1 / R_ii), then w_j -= x_i R_ij for j > i.  The reciprocal is the
+// diagonal of the R^{-1} that k_chol_inv writes (the correctly rounded 1 / R_ii).  Solving
+// the triangular system keeps the backward error of each row at the level of R's rounding;
+// multiplying by an explicitly inverted R adds the error of the inverse, which grows with
+// the condition number of R and costs A-orthogonality on ill-conditioned blocks.
+// One thread per row; the CTA's rows are staged in shared memory (row stride ld = m or m+1,
+// odd, so that a half-warp's float64 accesses fall in distinct banks).
+// ---------------------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(128)
+k_trsm_rows(MB<T> X, const double* __restrict__ R, const double* __restrict__ Rinv, int m,
+            int64_t n) {
+    extern __shared__ unsigned char smem_raw[];
+    double* xs = reinterpret_cast<double*>(smem_raw);
+    const int ld = m | 1;
+    const int rows = blockDim.x;
+    for (int64_t r0 = (int64_t)blockIdx.x * rows; r0 < n; r0 += (int64_t)gridDim.x * rows) {
+        for (int e = threadIdx.x; e < rows * m; e += blockDim.x) {
+            const int rr = e / m, cc = e - rr * m;
+            const int64_t row = r0 + rr;
+            const int b = cc / X.w;
+            xs[rr * ld + cc] = (row < n) ? (double)X.blk(b)[row * X.w + (cc - b * X.w)] : 0.0;
+        }
+        __syncthreads();
+        double* xr = xs + threadIdx.x * ld;
+        for (int i = 0; i < m; ++i) {
+            const double xi = xr[i] * __ldg(Rinv + (int64_t)i * m + i);
+            xr[i] = xi;
+            const double* Ri = R + (int64_t)i * m;
+            for (int j = i + 1; j < m; ++j) xr[j] = fma(-xi, __ldg(Ri + j), xr[j]);
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < rows * m; e += blockDim.x) {
+            const int rr = e / m, cc = e - rr * m;
+            const int64_t row = r0 + rr;
+            const int b = cc / X.w;
+            if (row < n) X.blk(b)[row * X.w + (cc - b * X.w)] = (T)xs[rr * ld + cc];
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------------------
 // x += V alpha, r -= (A V) alpha, partials of ||r||^2   (Algorithm 4 last three lines)
 // ---------------------------------------------------------------------------------------
 template <typename T>

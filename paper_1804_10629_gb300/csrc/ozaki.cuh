@@ -1,0 +1,734 @@
+// Float64-accurate tall-skinny contractions on the bf16 tensor cores (tcgen05, sm_103a).
+//
+// The CGS update W <- W - Q C of the A-orthonormalisation (Section 3.1, Section 4) is a
+// product of an n x P block by a small P x Q matrix.  GB300's float64 FMA pipe retires about
+// two FMAs per SM cycle, so in float64 this product runs twenty times below the HBM
+// roofline.  Here it runs as a split ("Ozaki") product on the bf16 tensor cores:
+//
+//   * each row i of X (P values) is scaled by its largest binade, 2^{e_i - 1022}, and its
+//     magnitudes cut into a 56-bit fixed-point integer F = sum_a x_a 2^{56-7a}, eight 7-bit
+//     slices x_a in [0, 127] carrying the sign of the value (exact in bf16);
+//   * each column q of C is cut the same way against its own binade 2^{f_q - 1022};
+//   * the slice products are integers below 2^14, so over K = P <= 64 terms and up to eight
+//     slice pairs (a, b) with a + b = g the fp32 accumulator of tcgen05.mma holds the exact
+//     group sum G_g = sum_{a+b=g} sum_k x_a[i,k] c_b[k,q] (|G_g| < 2^23);
+//   * the 36 pairs with a + b <= 9 form eight groups g = 2..9, each in its own TMEM
+//     accumulator (128 lanes = rows, Q columns); the dropped pairs and the truncation of F
+//     weigh at most about 2^-52 of max|X_i| max|C_q| per term, the size of one float64
+//     rounding of that term;
+//   * the epilogue combines the eight exact groups in 64-bit integers,
+//     V = sum_g G_g 2^{7(9-g)} (kept as V >> 7 below 2^62), converts V once to float64 and
+//     applies the scale and the subtraction with one fused multiply-add:
+//     OUT = Y - V 2^{e_i + f_q - 2100}.
+//
+// Tensor-core mechanics: A (X slices, 128 rows x K) and B (C slices, Q x K) sit in shared
+// memory in the canonical K-major no-swizzle layout of 8 x 16-byte core matrices (leading
+// byte offset = distance of core matrices along K, stride byte offset = along M / N); one
+// thread issues kind::f16 MMAs (bf16 x bf16 -> fp32, M = 128, N = Q, K = 16) into the
+// accumulators allocated in tensor memory, commits them to an mbarrier, and the epilogue
+// warps read the accumulators back with tcgen05.ld (warp w reads lanes 32 (w % 4) .. +31).
+// Every mbarrier wait is bounded: a wait that runs out sets bit 2 of *err; the CTA then
+// waits (bounded) for its outstanding MMAs, frees its tensor memory and returns.
+#pragma once
+
+#include <cstdint>
+
+#include "bulk.cuh"
+#include "kernels.cuh"
+
+namespace ekcg {
+namespace oz {
+
+constexpr int kThreads = 256;
+constexpr int kTile = 128;      // rows of X per tile (M of one MMA)
+constexpr int kSlices = 8;      // 7-bit slices of the 56-bit fixed-point magnitude
+constexpr int kGroups = 8;      // slice-pair groups g = a + b = 2..9
+constexpr int kKC = 32;         // columns of X sliced per stage (K per stage)
+
+// ---- tcgen05 / descriptor helpers ------------------------------------------------------
+// Shared-memory matrix descriptor, K-major, no swizzle: start address, leading byte offset
+// (K direction), stride byte offset (M / N direction), descriptor version 1 (bits 46-47).
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+// Instruction descriptor of kind::f16: fp32 accumulator (bits 4-5 = 1), A and B bf16 (bits
+// 7-9, 10-12 = 1), both K-major, N >> 3 at bits 17-22, M >> 4 at bits 24-28.
+__host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
+           ((uint32_t)(M >> 4) << 24);
+}
+__device__ __forceinline__ void tmem_alloc(uint32_t* slot, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     bulk::smem_addr(slot)),
+                 "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr),
+                 "r"(ncols)
+                 : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+// generic-proxy shared-memory writes -> visible to the tensor core (async proxy)
+__device__ __forceinline__ void fence_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
+                                         uint32_t idesc, uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+// arrive on the mbarrier once every MMA this thread issued before has completed
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+            bulk::smem_addr(bar))
+        : "memory");
+}
+// 32 lanes x 8 consecutive 32-bit columns: this thread's lane, columns taddr.col .. +7
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
+    uint32_t r[8];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7])
+        : "r"(taddr)
+        : "memory");
+#pragma unroll
+    for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
+__device__ __forceinline__ void tmem_wait_ld() {
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// ---- slicing ----------------------------------------------------------------------------
+// Biased float64 exponent (0 for zero and subnormal values, which are treated as zero).
+__device__ __forceinline__ int bexp(double x) {
+    return (int)((__double_as_longlong(x) >> 52) & 0x7FF);
+}
+// 56-bit fixed-point magnitude of x against the binade 2^{e - 1022} (e >= bexp(x)):
+// floor(|x| 2^{56 - (e - 1022)}), below 2^56.
+__device__ __forceinline__ uint64_t fixed56(double x, int e) {
+    const uint64_t u = (uint64_t)__double_as_longlong(x);
+    const int ex = (int)((u >> 52) & 0x7FF);
+    if (ex == 0) return 0;
+    const uint64_t m = (u & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+    const int sh = ex - e + 3;   // <= 3
+    if (sh >= 0) return m << sh;
+    return (sh > -64) ? (m >> (-sh)) : 0;
+}
+// bf16 bit pattern of the signed 7-bit slice: the float 2^23 + s (sign folded into the bit
+// pattern) plus -+2^23 is exactly +-s; its upper 16 bits are the bf16 value.
+__device__ __forceinline__ uint32_t slice_f32_bits(uint32_t s7, uint32_t magic_sign,
+                                                   float undo) {
+    return __float_as_uint(__uint_as_float((s7 & 127u) | magic_sign) + undo);
+}
+// slice a (0-based: bits 49 - 7a .. 55 - 7a of F) as a float bit pattern
+__device__ __forceinline__ uint32_t slice_bits(uint64_t F, int a, uint32_t ms, float undo) {
+    const uint32_t hi = (uint32_t)(F >> 32), lo = (uint32_t)F;
+    uint32_t s;
+    switch (a) {
+        case 0: s = hi >> 17; break;
+        case 1: s = hi >> 10; break;
+        case 2: s = hi >> 3; break;
+        case 3: s = __funnelshift_r(lo, hi, 28); break;
+        case 4: s = lo >> 21; break;
+        case 5: s = lo >> 14; break;
+        case 6: s = lo >> 7; break;
+        default: s = lo; break;
+    }
+    return slice_f32_bits(s, ms, undo);
+}
+__device__ __forceinline__ uint32_t sign_magic(bool neg) {
+    return 0x4B000000u | (neg ? 0x80000000u : 0u);
+}
+__device__ __forceinline__ float sign_undo(bool neg) { return neg ? 8388608.f : -8388608.f; }
+// two bf16 (the upper halves of two float bit patterns) in one word, first in the low half
+__device__ __forceinline__ uint32_t pack_bf16(uint32_t f0, uint32_t f1) {
+    return __byte_perm(f0, f1, 0x7632);
+}
+
+// ---- the update -------------------------------------------------------------------------
+// One persistent CTA per SM, warp-specialised:
+//   warps 0-7  (slicers): per 128-row tile, load the tile's X values (each thread half a row,
+//              P/2 values), take the row binade, and cut the values into the eight slices,
+//              one K-step (16 columns) at a time, into a ring of kStages shared stages;
+//   warp 8     (MMA): one thread issues the 36 pair MMAs of every K-step into one of two
+//              tensor-memory accumulator sets and commits each stage back to the slicers
+//              and each finished tile to the epilogue;
+//   warps 9-12 (epilogue): lane quarter w % 4 reads its 32 rows of the finished set,
+//              combines the eight groups, applies scale and subtraction and writes OUT.
+// mbarriers: full[s] / empty[s] per ring stage, acc_full[b] / acc_empty[b] and
+// erow_full[b] per accumulator set.  Each wait is bounded; a wait that runs out sets a
+// shared abort word that every role checks, so all roles leave their loops.
+constexpr int kSlicerWarps = 8;
+constexpr int kMmaWarp = 8;
+constexpr int kEpiWarp0 = 9;
+constexpr int kUpdThreads = 13 * 32;
+constexpr int kKS = 16;          // columns of X per ring stage (one MMA K-step)
+constexpr int kStages = 4;
+
+template <int P, int Q>
+struct UpdShape {
+    static_assert(P % 16 == 0 && P >= 16 && P <= 64, "P: multiple of 16, at most 64");
+    static_assert(Q == 16 || Q == 32, "Q: 16 or 32");
+    static constexpr int kSliceStage = kTile * kKS * 2;            // one slice of one stage
+    static constexpr int kStageBytes = kSlices * kSliceStage;      // 32 KB
+    static constexpr int kSliceB = Q * P * 2;                      // one slice of C
+    static constexpr int kOffB = kStages * kStageBytes;
+    static constexpr int kSmem = kOffB + kSlices * kSliceB + 1024;  // + alignment slack
+    static constexpr int kLboA = (kTile / 8) * 128;                // next 8 columns of A
+    static constexpr int kLboB = (Q / 8) * 128;                    // next 8 columns of B
+    static constexpr uint32_t kAcc = (uint32_t)(kGroups * Q);      // columns of one set
+    static constexpr uint32_t kCols = 2 * kAcc;                    // two sets
+    static constexpr int kKSteps = P / kKS;
+};
+
+__device__ __forceinline__ bool wait_or_abort(uint64_t* bar, uint32_t parity,
+                                              volatile int* abort) {
+    const long long t0 = clock64();
+    while (!bulk::mbar_test(bar, parity)) {
+        if (*abort) return false;
+        if (clock64() - t0 > bulk::kWaitCycles) {
+            *abort = 1;
+            return false;
+        }
+    }
+    return true;
+}
+// named barrier `id` over `count` threads that also returns the OR of v over them
+__device__ __forceinline__ bool bar_or(int id, int count, bool v) {
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.u32 p, %1, 0;\n\t"
+        "barrier.red.or.pred q, %2, %3, p;\n\t"
+        "selp.u32 %0, 1, 0, q;\n\t}"
+        : "=r"(r)
+        : "r"((uint32_t)v), "r"(id), "r"(count)
+        : "memory");
+    return r != 0;
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bulk::smem_addr(bar))
+                 : "memory");
+}
+
+// OUT = Y - X C (beta_on = 1: the CGS update) or OUT = X C (beta_on = 0: the product with
+// R^{-1}) with X = the P columns of X.count blocks (each X.w a multiple of 8), C P x Q
+// (row-major, ldc = Q), Y and OUT single n x Q blocks.  OUT may be Y, and OUT may be X
+// itself (P = Q, one block): a tile's rows are read by the slicers before the MMAs of that
+// tile complete, and written by the epilogue only after.
+template <int P, int Q>
+__global__ void __launch_bounds__(kUpdThreads, 1)
+k_oz_update(MB<const double> X, const double* __restrict__ C, MB<const double> Y,
+            MB<double> OUT, int64_t n, int beta_on, int* err) {
+    using S = UpdShape<P, Q>;
+    extern __shared__ __align__(1024) unsigned char oz_raw[];
+    unsigned char* sm = oz_raw + ((1024 - (bulk::smem_addr(oz_raw) & 1023)) & 1023);
+    __shared__ __align__(8) uint64_t full[kStages], empty[kStages];
+    __shared__ __align__(8) uint64_t acc_full[2], acc_empty[2], erow_full[2], fin;
+    __shared__ uint32_t tslot;
+    __shared__ int erow[2][kTile];
+    __shared__ int fcol[Q];
+    __shared__ volatile int abort_flag;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint32_t sA = bulk::smem_addr(sm), sB = sA + S::kOffB;
+
+    if (warp == 0) tmem_alloc(&tslot, S::kCols);
+    if (tid == 0) {
+        for (int i = 0; i < kStages; ++i) {
+            bulk::mbar_init(&full[i], kSlicerWarps);
+            bulk::mbar_init(&empty[i], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            bulk::mbar_init(&acc_full[b], 1);
+            bulk::mbar_init(&acc_empty[b], 4);
+            bulk::mbar_init(&erow_full[b], kSlicerWarps);
+        }
+        bulk::mbar_init(&fin, 1);
+        abort_flag = 0;
+        bulk::fence_barrier_init();
+    }
+    // C: column binades, then the slices of every entry into the B operand (N = Q x K = P)
+    if (tid < Q) {
+        int f = 0;
+        for (int k = 0; k < P; ++k) f = max(f, bexp(C[(int64_t)k * Q + tid]));
+        fcol[tid] = f;
+    }
+    __syncthreads();
+    for (int e = tid; e < P * Q; e += blockDim.x) {
+        const int k = e / Q, q = e - k * Q;
+        const double c = C[(int64_t)k * Q + q];
+        const uint64_t F = fixed56(c, fcol[q]);
+        const bool neg = (__double_as_longlong(c) >> 63) != 0;
+        const uint32_t ms = sign_magic(neg);
+        const float undo = sign_undo(neg);
+        const int off = ((k >> 3) * (Q / 8) + (q >> 3)) * 128 + (q & 7) * 16 + (k & 7) * 2;
+#pragma unroll
+        for (int a = 0; a < kSlices; ++a)
+            *reinterpret_cast<uint16_t*>(sm + S::kOffB + a * S::kSliceB + off) =
+                (uint16_t)(slice_bits(F, a, ms, undo) >> 16);
+    }
+    fence_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tbase = tslot;
+    const int64_t ntiles = (n + kTile - 1) / kTile;
+
+    if (warp < kSlicerWarps) {
+        // ---- slicers: thread = (row r, half h); the half holds column groups h + 2j
+        const int r = warp * 16 + (lane & 15), h = lane >> 4;
+        int stage = 0;
+        int lt = 0;
+        for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++lt) {
+            const int buf = lt & 1;
+            if (lt >= 2 && !wait_or_abort(&acc_empty[buf], ((lt >> 1) - 1) & 1, &abort_flag))
+                break;
+            const int64_t i = tile * kTile + r;
+            double xv[P / 2];
+#pragma unroll
+            for (int j = 0; j < P / 16; ++j) {
+                const int col = (h + 2 * j) * 8, b = col / X.w;
+                const double2* src =
+                    reinterpret_cast<const double2*>(X.blk(b) + i * X.w + (col - b * X.w));
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const double2 v = (i < n) ? src[u] : make_double2(0.0, 0.0);
+                    xv[j * 8 + 2 * u] = v.x;
+                    xv[j * 8 + 2 * u + 1] = v.y;
+                }
+            }
+            int e = 0;
+#pragma unroll
+            for (int u = 0; u < P / 2; ++u) e = max(e, bexp(xv[u]));
+            e = max(e, __shfl_xor_sync(0xffffffffu, e, 16));
+            if (h == 0) erow[buf][r] = e;
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&erow_full[buf]);
+            bool ok = true;
+#pragma unroll
+            for (int j = 0; j < P / 16; ++j) {
+                // K-step j = column groups 2j, 2j+1; this thread holds group 2j + h
+                const int slot = stage % kStages, use = stage / kStages;
+                if (use >= 1 && !wait_or_abort(&empty[slot], (use - 1) & 1, &abort_flag)) {
+                    ok = false;
+                    break;
+                }
+                uint64_t F[8];
+                uint32_t ms[8];
+                float undo[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const double x = xv[j * 8 + u];
+                    F[u] = fixed56(x, e);
+                    const bool neg = (__double_as_longlong(x) >> 63) != 0;
+                    ms[u] = sign_magic(neg);
+                    undo[u] = sign_undo(neg);
+                }
+                unsigned char* dst = sm + slot * S::kStageBytes +
+                                     (h * (kTile / 8) + (r >> 3)) * 128 + (r & 7) * 16;
+#pragma unroll
+                for (int a = 0; a < kSlices; ++a) {
+                    uint4 v;
+                    v.x = pack_bf16(slice_bits(F[0], a, ms[0], undo[0]),
+                                    slice_bits(F[1], a, ms[1], undo[1]));
+                    v.y = pack_bf16(slice_bits(F[2], a, ms[2], undo[2]),
+                                    slice_bits(F[3], a, ms[3], undo[3]));
+                    v.z = pack_bf16(slice_bits(F[4], a, ms[4], undo[4]),
+                                    slice_bits(F[5], a, ms[5], undo[5]));
+                    v.w = pack_bf16(slice_bits(F[6], a, ms[6], undo[6]),
+                                    slice_bits(F[7], a, ms[7], undo[7]));
+                    *reinterpret_cast<uint4*>(dst + a * S::kSliceStage) = v;
+                }
+                fence_async_smem();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&full[slot]);
+                ++stage;
+            }
+            if (!ok) break;
+        }
+    } else if (warp == kMmaWarp) {
+        // ---- MMA issue (one thread)
+        if (lane == 0) {
+            constexpr uint32_t idesc = idesc_bf16_f32(kTile, Q);
+            int stage = 0;
+            int lt = 0;
+            for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++lt) {
+                const int buf = lt & 1;
+                if (lt >= 2 &&
+                    !wait_or_abort(&acc_empty[buf], ((lt >> 1) - 1) & 1, &abort_flag))
+                    break;
+                tc_fence_after();
+                const uint32_t dacc = tbase + (uint32_t)buf * S::kAcc;
+                bool ok = true;
+                for (int j = 0; j < S::kKSteps; ++j) {
+                    const int slot = stage % kStages, use = stage / kStages;
+                    if (!wait_or_abort(&full[slot], use & 1, &abort_flag)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+#pragma unroll 1
+                    for (int a = 1; a <= kSlices; ++a) {
+                        const uint64_t ad = smem_desc(
+                            sA + slot * S::kStageBytes + (a - 1) * S::kSliceStage, S::kLboA, 128);
+#pragma unroll 1
+                        for (int b = 1; b <= kGroups + 1 - a; ++b) {
+                            const uint64_t bd = smem_desc(
+                                sB + (b - 1) * S::kSliceB + j * 2 * S::kLboB, S::kLboB, 128);
+                            mma_bf16(dacc + (uint32_t)((a + b - 2) * Q), ad, bd, idesc,
+                                     (j > 0 || a > 1) ? 1u : 0u);
+                        }
+                    }
+                    mma_commit(&empty[slot]);
+                    ++stage;
+                }
+                if (!ok) break;
+                mma_commit(&acc_full[buf]);
+            }
+            // every MMA issued has completed before the tensor memory is released
+            mma_commit(&fin);
+            bulk::mbar_wait(&fin, 0);
+        }
+        __syncwarp();
+    } else {
+        // ---- epilogue: quarter qd = warp % 4, rows 32 qd + lane of the tile
+        const int qd = warp & 3;
+        const int m = qd * 32 + lane;
+        int lt = 0;
+        for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++lt) {
+            const int buf = lt & 1, use = lt >> 1;
+            if (!wait_or_abort(&acc_full[buf], use & 1, &abort_flag)) break;
+            if (!wait_or_abort(&erow_full[buf], use & 1, &abort_flag)) break;
+            tc_fence_after();
+            const int64_t ri = tile * kTile + m;
+            const int er = erow[buf][m];
+            const uint32_t taddr = tbase + ((uint32_t)(qd * 32) << 16) + (uint32_t)buf * S::kAcc;
+#pragma unroll 1
+            for (int col0 = 0; col0 < Q; col0 += 8) {
+                float g[kGroups][8];
+#pragma unroll
+                for (int gi = 0; gi < kGroups; ++gi)
+                    tmem_ld8(taddr + (uint32_t)(gi * Q + col0), g[gi]);
+                tmem_wait_ld();
+                if (ri < n) {
+                    const double* yr = beta_on ? Y.blk(0) + ri * Y.w + col0 : nullptr;
+                    double* orow = OUT.blk(0) + ri * OUT.w + col0;
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        long long hi = 0, lo = 0;
+#pragma unroll
+                        for (int gi = 0; gi < 4; ++gi)
+                            hi = hi * 128 + (long long)__float2int_rn(g[gi][u]);
+#pragma unroll
+                        for (int gi = 4; gi < 8; ++gi)
+                            lo = lo * 128 + (long long)__float2int_rn(g[gi][u]);
+                        const long long v7 = hi * (1ll << 21) + (lo >> 7);
+                        const int ex = er + fcol[col0 + u] - 1077;
+                        const double scale =
+                            ex < 1 ? 0.0
+                                   : (ex > 2046 ? __longlong_as_double(0x7FF0000000000000ll)
+                                                : __longlong_as_double((long long)ex << 52));
+                        orow[u] = fma((double)(beta_on ? -v7 : v7), scale,
+                                      beta_on ? yr[u] : 0.0);
+                    }
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&acc_empty[buf]);
+        }
+    }
+    __syncthreads();
+    if (abort_flag && tid == 0) atomicOr(err, 4);
+    if (warp == 0) {
+        tc_fence_after();
+        tmem_dealloc(tbase, S::kCols);
+    }
+}
+
+// ---- the Gram product ---------------------------------------------------------------
+// C = X^T Y over the n rows (CGS coefficients Q^T (A W), the A-CholQR Gram W^T (A W)):
+// X n x P (P <= 64, padded to the MMA's M = 64), Y n x Q (Q = 16 or 32).  The contraction
+// runs over rows, in tiles of 128 rows: every column of X and of Y is scaled by its binade
+// over the tile (e_p, f_q), so a tile's eight groups are exact in fp32 (<= 8 pairs x 128
+// rows x 127^2 < 2^24), and the epilogue adds the tile's V 2^{e_p + f_q - 2100} into a
+// float64 accumulator per output held in registers across the CTA's tiles.  Each CTA writes
+// its P x Q partial sum; k_gram_reduce adds the partials in CTA order.
+//   warps 0 .. 2 nb - 1 (slicers, nb = ceil((P + Q) / 32) column blocks): lane = column,
+//              warp = (column block, row parity); pass 1 takes the column binades of the
+//              tile (a shared max over the two row parities), pass 2 cuts 8 rows x 1 column
+//              per thread and K-step into the ring;
+//   warp 6     (MMA): 36 pair MMAs (M = 64, N = Q, K = 16) per K-step;
+//   warps 8-11 (epilogue): M = 64 keeps rows 16 q' .. 16 q' + 15 of D in lanes 0-15 of lane
+//              quarter q', so lanes 0-15 of warp 8 + q' own the outputs p = 16 q' + lane.
+constexpr int kGramThreads = 12 * 32;
+constexpr int kGramMmaWarp = 6;
+constexpr int kGramEpiWarp0 = 8;
+constexpr int kGramRows = 128;       // rows per tile (binade scope, exact fp32 sums)
+constexpr int kGramStages = 6;
+
+template <int P, int Q>
+struct GramShape {
+    static_assert(P % 16 == 0 && P >= 16 && P <= 64, "P: multiple of 16, at most 64");
+    static_assert(Q == 16 || Q == 32, "Q: 16 or 32");
+    static constexpr int kM = 64;
+    static constexpr int kSliceA = kM * kKS * 2;                   // 2 KB
+    static constexpr int kSliceB = Q * kKS * 2;
+    static constexpr int kStageBytes = kSlices * (kSliceA + kSliceB);
+    static constexpr int kOffB = kSlices * kSliceA;                // B inside a stage
+    static constexpr int kSmem = kGramStages * kStageBytes + 1024;
+    static constexpr int kLboA = (kM / 8) * 128;
+    static constexpr int kLboB = (Q / 8) * 128;
+    static constexpr uint32_t kAcc = (uint32_t)(kGroups * Q);
+    static constexpr uint32_t kCols = 2 * kAcc;
+    static constexpr int kT = P + Q;                               // columns sliced per row
+    static constexpr int kNB = (kT + 31) / 32;                     // column blocks
+    static constexpr int kSlicers = 2 * kNB;                       // slicer warps (<= 6)
+    static constexpr int kKSteps = kGramRows / kKS;                // 8
+};
+
+// partials[cta * 4096 + p * Q + q] = this CTA's share of (X^T Y)[p, q]
+template <int P, int Q>
+__global__ void __launch_bounds__(kGramThreads, 1)
+k_oz_gram(MB<const double> X, MB<const double> Y, int64_t n, double* __restrict__ partials,
+          int* err) {
+    using S = GramShape<P, Q>;
+    extern __shared__ __align__(1024) unsigned char oz_raw[];
+    unsigned char* sm = oz_raw + ((1024 - (bulk::smem_addr(oz_raw) & 1023)) & 1023);
+    __shared__ __align__(8) uint64_t full[kGramStages], empty[kGramStages];
+    __shared__ __align__(8) uint64_t acc_full[2], acc_empty[2], cexp_full[2], fin;
+    __shared__ uint32_t tslot;
+    __shared__ int cexp[2][S::kT];          // tile binades: X columns, then Y columns
+    __shared__ int cmax[2][S::kNB * 32];    // per row parity, pass 1
+    __shared__ volatile int abort_flag;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint32_t sbase = bulk::smem_addr(sm);
+
+    if (warp == 0) tmem_alloc(&tslot, S::kCols);
+    if (tid == 0) {
+        for (int i = 0; i < kGramStages; ++i) {
+            bulk::mbar_init(&full[i], S::kSlicers);
+            bulk::mbar_init(&empty[i], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            bulk::mbar_init(&acc_full[b], 1);
+            bulk::mbar_init(&acc_empty[b], 4);
+            bulk::mbar_init(&cexp_full[b], S::kSlicers);
+        }
+        bulk::mbar_init(&fin, 1);
+        abort_flag = 0;
+        bulk::fence_barrier_init();
+    }
+    // the ring starts zeroed: rows p >= P of the A operand stay zero
+    for (int e = tid * 16; e < kGramStages * S::kStageBytes; e += blockDim.x * 16)
+        *reinterpret_cast<uint4*>(sm + e) = make_uint4(0u, 0u, 0u, 0u);
+    fence_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tbase = tslot;
+    const int64_t ntiles = (n + kGramRows - 1) / kGramRows;
+
+    if (warp < S::kSlicers) {
+        // ---- slicers: column c = 32 (warp / 2) + lane (X columns first), row parity warp % 2
+        const int cb = warp >> 1, par = warp & 1;
+        const int c = cb * 32 + lane;
+        const bool active = c < S::kT;
+        const bool isx = c < P;
+        const int cc = isx ? c : c - P;                   // column inside X or Y
+        const MB<const double>& M = isx ? X : Y;
+        const int blk = active ? cc / M.w : 0, cw = active ? cc - blk * M.w : 0;
+        const double* base = M.blk(blk) + cw;
+        const int64_t ld = M.w;
+        int stage = 0;
+        int lt = 0;
+        bool failed = false;   // the slicer warps leave together (they share named barriers)
+        for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++lt) {
+            const int buf = lt & 1;
+            if (lt >= 2 && !failed &&
+                !wait_or_abort(&acc_empty[buf], ((lt >> 1) - 1) & 1, &abort_flag))
+                failed = true;
+            if (bar_or(1, S::kSlicers * 32, failed || abort_flag)) break;
+            const int64_t r0 = tile * kGramRows;
+            // pass 1: binade of the column over the tile (this parity's row groups)
+            int e = 0;
+            if (active) {
+                for (int rg = par; rg < kGramRows / 8; rg += 2) {
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        const int64_t row = r0 + rg * 8 + u;
+                        if (row < n) e = max(e, bexp(base[row * ld]));
+                    }
+                }
+            }
+            cmax[par][cb * 32 + lane] = e;
+            asm volatile("bar.sync 1, %0;" ::"r"(S::kSlicers * 32) : "memory");
+            e = max(cmax[0][cb * 32 + lane], cmax[1][cb * 32 + lane]);
+            if (par == 0 && active) cexp[buf][c] = e;
+            asm volatile("bar.sync 1, %0;" ::"r"(S::kSlicers * 32) : "memory");
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&cexp_full[buf]);
+            // pass 2: K-step ks = row groups 2 ks, 2 ks + 1; this warp holds group 2 ks + par
+            for (int ks = 0; ks < S::kKSteps; ++ks) {
+                const int slot = stage % kGramStages, use = stage / kGramStages;
+                ++stage;
+                if (failed) continue;
+                if (use >= 1 && !wait_or_abort(&empty[slot], (use - 1) & 1, &abort_flag)) {
+                    failed = true;
+                    continue;
+                }
+                if (active) {
+                    const int64_t rowb = r0 + (2 * ks + par) * 8;
+                    uint64_t F[8];
+                    uint32_t ms[8];
+                    float undo[8];
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        const double x = (rowb + u < n) ? base[(rowb + u) * ld] : 0.0;
+                        F[u] = fixed56(x, e);
+                        const bool neg = (__double_as_longlong(x) >> 63) != 0;
+                        ms[u] = sign_magic(neg);
+                        undo[u] = sign_undo(neg);
+                    }
+                    unsigned char* dst =
+                        sm + slot * S::kStageBytes +
+                        (isx ? (par * (S::kM / 8) + (cc >> 3)) * 128
+                             : S::kOffB + (par * (Q / 8) + (cc >> 3)) * 128) +
+                        (cc & 7) * 16;
+                    const int sstride = isx ? S::kSliceA : S::kSliceB;
+#pragma unroll
+                    for (int a = 0; a < kSlices; ++a) {
+                        uint4 v;
+                        v.x = pack_bf16(slice_bits(F[0], a, ms[0], undo[0]),
+                                        slice_bits(F[1], a, ms[1], undo[1]));
+                        v.y = pack_bf16(slice_bits(F[2], a, ms[2], undo[2]),
+                                        slice_bits(F[3], a, ms[3], undo[3]));
+                        v.z = pack_bf16(slice_bits(F[4], a, ms[4], undo[4]),
+                                        slice_bits(F[5], a, ms[5], undo[5]));
+                        v.w = pack_bf16(slice_bits(F[6], a, ms[6], undo[6]),
+                                        slice_bits(F[7], a, ms[7], undo[7]));
+                        *reinterpret_cast<uint4*>(dst + a * sstride) = v;
+                    }
+                }
+                fence_async_smem();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&full[slot]);
+            }
+        }
+    } else if (warp == kGramMmaWarp) {
+        if (lane == 0) {
+            constexpr uint32_t idesc = idesc_bf16_f32(S::kM, Q);
+            int stage = 0;
+            int lt = 0;
+            for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++lt) {
+                const int buf = lt & 1;
+                if (lt >= 2 &&
+                    !wait_or_abort(&acc_empty[buf], ((lt >> 1) - 1) & 1, &abort_flag))
+                    break;
+                tc_fence_after();
+                const uint32_t dacc = tbase + (uint32_t)buf * S::kAcc;
+                bool ok = true;
+                for (int ks = 0; ks < S::kKSteps; ++ks) {
+                    const int slot = stage % kGramStages, use = stage / kGramStages;
+                    if (!wait_or_abort(&full[slot], use & 1, &abort_flag)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t st = sbase + slot * S::kStageBytes;
+#pragma unroll 1
+                    for (int a = 1; a <= kSlices; ++a) {
+                        const uint64_t ad = smem_desc(st + (a - 1) * S::kSliceA, S::kLboA, 128);
+#pragma unroll 1
+                        for (int b = 1; b <= kGroups + 1 - a; ++b) {
+                            const uint64_t bd = smem_desc(
+                                st + S::kOffB + (b - 1) * S::kSliceB, S::kLboB, 128);
+                            mma_bf16(dacc + (uint32_t)((a + b - 2) * Q), ad, bd, idesc,
+                                     (ks > 0 || a > 1) ? 1u : 0u);
+                        }
+                    }
+                    mma_commit(&empty[slot]);
+                    ++stage;
+                }
+                if (!ok) break;
+                mma_commit(&acc_full[buf]);
+            }
+            mma_commit(&fin);
+            bulk::mbar_wait(&fin, 0);
+        }
+        __syncwarp();
+    } else if (warp >= kGramEpiWarp0) {
+        // ---- epilogue: outputs p = 16 qd + lane (lane < 16), all Q columns
+        const int qd = warp & 3;
+        const int p = qd * 16 + (lane & 15);
+        const bool own = lane < 16 && p < P;
+        double acc[Q];
+#pragma unroll
+        for (int q = 0; q < Q; ++q) acc[q] = 0.0;
+        int lt = 0;
+        for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++lt) {
+            const int buf = lt & 1, use = lt >> 1;
+            if (!wait_or_abort(&acc_full[buf], use & 1, &abort_flag)) break;
+            if (!wait_or_abort(&cexp_full[buf], use & 1, &abort_flag)) break;
+            tc_fence_after();
+            const int ep = own ? cexp[buf][p] : 0;
+            const uint32_t taddr = tbase + ((uint32_t)(qd * 32) << 16) + (uint32_t)buf * S::kAcc;
+#pragma unroll
+            for (int col0 = 0; col0 < Q; col0 += 8) {
+                float g[kGroups][8];
+#pragma unroll
+                for (int gi = 0; gi < kGroups; ++gi)
+                    tmem_ld8(taddr + (uint32_t)(gi * Q + col0), g[gi]);
+                tmem_wait_ld();
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    long long hi = 0, lo = 0;
+#pragma unroll
+                    for (int gi = 0; gi < 4; ++gi)
+                        hi = hi * 128 + (long long)__float2int_rn(g[gi][u]);
+#pragma unroll
+                    for (int gi = 4; gi < 8; ++gi)
+                        lo = lo * 128 + (long long)__float2int_rn(g[gi][u]);
+                    const long long v7 = hi * (1ll << 21) + (lo >> 7);
+                    const int ex = ep + cexp[buf][P + col0 + u] - 1077;
+                    const double scale =
+                        ex < 1 ? 0.0
+                               : (ex > 2046 ? __longlong_as_double(0x7FF0000000000000ll)
+                                            : __longlong_as_double((long long)ex << 52));
+                    acc[col0 + u] = fma((double)v7, scale, acc[col0 + u]);
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&acc_empty[buf]);
+        }
+        if (own) {
+            double* out = partials + (int64_t)blockIdx.x * 4096 + p * Q;
+#pragma unroll
+            for (int q = 0; q < Q; ++q) out[q] = acc[q];
+        }
+    }
+    __syncthreads();
+    if (abort_flag && tid == 0) atomicOr(err, 4);
+    if (warp == 0) {
+        tc_fence_after();
+        tmem_dealloc(tbase, S::kCols);
+    }
+}
+
+}  // namespace oz
+}  // namespace ekcg

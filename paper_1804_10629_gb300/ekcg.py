@@ -25,13 +25,14 @@ VARIANT = {"sre": 0, "sre2": 1, "msdo": 2}
 BASIS = {"sstep": 0, "ca5": 1, "ca7": 2, "restructured": 3}
 ORTH = {"acholqr": 0, "precholqr": 1}
 PRECISION = {"fp64": 0, "fp32_ir": 1}
+CONTRACTION = {"fp64": 0, "split": 1}
 
 
 class ekcg_opts(ctypes.Structure):
     _fields_ = [("variant", c_int), ("basis", c_int), ("orth", c_int), ("precision", c_int),
                 ("max_s", c_int), ("max_blocks", c_int), ("max_basis_bytes", c_int64),
                 ("breakdown_tol", c_double), ("inner_tol", c_double), ("max_refine", c_int),
-                ("profile", c_int)]
+                ("profile", c_int), ("contraction", c_int)]
 
 
 class EkcgError(RuntimeError):
@@ -87,6 +88,11 @@ def _declare(L):
     L.ekcg_gram_noalloc.argtypes = [c_int64, c_void_p, c_int, c_void_p, c_int, c_void_p,
                                     c_void_p]
     L.ekcg_gram_noalloc.restype = c_int
+    L.ekcg_sub_xc.argtypes = [c_void_p, c_void_p, c_int, c_void_p, c_void_p, c_int,
+                              c_void_p, c_int]
+    L.ekcg_sub_xc.restype = c_int
+    L.ekcg_gram_with.argtypes = [c_void_p, c_void_p, c_int, c_void_p, c_int, c_void_p, c_int]
+    L.ekcg_gram_with.restype = c_int
     L.ekcg_spmm.argtypes = [c_void_p, c_void_p, c_void_p, c_int]
     L.ekcg_spmm.restype = c_int
     L.ekcg_permute.argtypes = [c_void_p, c_void_p, c_void_p, c_int]
@@ -283,6 +289,18 @@ def ekcg_gram_noalloc(n, X, p, Y, q, C, stream=None):
                                    c_void_p(stream) if stream else None), "ekcg_gram_noalloc")
 
 
+def ekcg_sub_xc(ctx, X, p, C, Y, q, OUT, contraction="fp64"):
+    """OUT = Y - X C (device tensors, row-major); contraction "fp64" or "split"."""
+    _check(lib().ekcg_sub_xc(ctx, _ptr(X), int(p), _ptr(C), _ptr(Y), int(q), _ptr(OUT),
+                             CONTRACTION[contraction]), "ekcg_sub_xc")
+
+
+def ekcg_gram_with(ctx, X, p, Y, q, C, contraction="fp64"):
+    """C = X^T Y (device tensors, row-major); contraction "fp64" or "split"."""
+    _check(lib().ekcg_gram_with(ctx, _ptr(X), int(p), _ptr(Y), int(q), _ptr(C),
+                                CONTRACTION[contraction]), "ekcg_gram_with")
+
+
 def ekcg_spmm(ctx, W, U, w):
     _check(lib().ekcg_spmm(ctx, _ptr(W), _ptr(U), int(w)), "ekcg_spmm")
 
@@ -316,7 +334,7 @@ class Solver:
     def __init__(self, A, t, part, variant="sre", basis="sstep", orth="acholqr",
                  precision="fp64", max_s=8, max_blocks=0, max_basis_bytes=0,
                  breakdown_tol=1e-14, inner_tol=1e-4, max_refine=30, profile=False,
-                 stream=None):
+                 stream=None, contraction="fp64"):
         import torch
         o = ekcg_default_opts()
         o.variant, o.basis, o.orth = VARIANT[variant], BASIS[basis], ORTH[orth]
@@ -324,6 +342,7 @@ class Solver:
         o.max_s, o.max_blocks, o.max_basis_bytes = max_s, max_blocks, max_basis_bytes
         o.breakdown_tol, o.inner_tol, o.max_refine = breakdown_tol, inner_tol, max_refine
         o.profile = int(bool(profile))
+        o.contraction = CONTRACTION[contraction]
         if stream is None:
             stream = torch.cuda.current_stream().cuda_stream
         self.n = int(A.n)

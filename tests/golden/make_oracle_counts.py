@@ -5,7 +5,15 @@ reference arm of bench.py time a bounded sample of s-step iterations and scale i
 solve, and give the GPU tests a full-size count to compare with.
 
 Usage: python tests/golden/make_oracle_counts.py [workload ...]   (ani3d, sky3d, poisson2d)
+       python tests/golden/make_oracle_counts.py --s S workload       (one s of a workload)
        python tests/golden/make_oracle_counts.py --perturbed SEED workload
+       python tests/golden/make_oracle_counts.py diff2d
+
+The diff2d form records the differentiable workload (2D diffusion 512^2, kappa = exp of a
+Gaussian random field, t = 16, s = 3): the solve for the target x* (field seed 5, b = 1),
+the forward solve x (field seed 4, b = 1), the adjoint solve A lambda = x - x* and the
+gradient dL/dlog kappa, with iteration counts, the first 21 residual norms and the values of
+x, lambda and the gradient at 256 fixed sample rows (plus their 2-norms and max-norms).
 
 The second form solves with b multiplied entrywise by (1 + 1e-15 xi), xi standard normal
 from the given seed, and stores the iteration count under "<key>/perturbed/<SEED>": the
@@ -59,9 +67,76 @@ def perturbed(seed, name):
         print(key, res.iters, res.status, f"{dt:.1f}s", flush=True)
 
 
+DIFF2D_N, DIFF2D_T, DIFF2D_S = 512, 16, 3
+DIFF2D_SAMPLES = 256
+
+
+def diff2d_sample_rows(n):
+    """256 fixed sample rows of the 512^2 grid (natural order), spread over the whole grid."""
+    return np.unique(np.linspace(0, n - 1, DIFF2D_SAMPLES).round().astype(np.int64))
+
+
+def solve_record(A, b, part, t, s):
+    t0 = time.time()
+    res = o.solve(A, b, part, t, s, tol=1e-8, maxit=20000, variant="sre")
+    dt = time.time() - t0
+    relres = float(np.linalg.norm(b - A.to_scipy() @ res.x) / np.linalg.norm(b))
+    rec = dict(iters=res.iters, status=res.status, relres=relres, seconds=round(dt, 2),
+               cores=len(os.sched_getaffinity(0)), hist=[float(h) for h in res.hist[:21]])
+    return res, rec
+
+
+def diff2d():
+    """Forward, target and adjoint solves and the log-kappa gradient of the differentiable
+    workload, all by the oracle."""
+    N, t, s = DIFF2D_N, DIFF2D_T, DIFF2D_S
+    lk = wl.kappa_gaussian_field2d(N, seed=4, corr=16.0)
+    lk_star = wl.kappa_gaussian_field2d(N, seed=5, corr=16.0)
+    part = wl.partition_boxes((N, N), t)
+    b = np.ones(N * N)
+    rows = diff2d_sample_rows(N * N)
+    A_star = wl.stencil_matrix((N, N), kappa=np.exp(lk_star))
+    res_star, rec_star = solve_record(A_star, b, part, t, s)
+    A = wl.stencil_matrix((N, N), kappa=np.exp(lk))
+    res_x, rec_x = solve_record(A, b, part, t, s)
+    g = res_x.x - res_star.x
+    res_l, rec_l = solve_record(A, g, part, t, s)
+    grad = o.diffusion2d_grad_logkappa(lk.ravel(), N, N, res_l.x, res_x.x)
+
+    def sample(v):
+        return dict(values=[float(v[i]) for i in rows], norm2=float(np.linalg.norm(v)),
+                    norminf=float(np.max(np.abs(v))))
+
+    key = f"diff2d/N{N}/t{t}/s{s}/sre/sstep/fp64"
+    rec_star.update(x=sample(res_star.x))
+    rec_x.update(x=sample(res_x.x))
+    rec_l.update(x=sample(res_l.x))
+    store(key + "/target", rec_star)
+    store(key + "/forward", rec_x)
+    store(key + "/adjoint", rec_l)
+    store(key + "/grad_logkappa", dict(sample(grad), rows=[int(i) for i in rows],
+                                       loss=float(0.5 * g @ g)))
+    print(key, rec_star["iters"], rec_x["iters"], rec_l["iters"], flush=True)
+
+
+def one_s(s, name):
+    cfg = RUNS[name]
+    p = cfg["make"]()
+    _, rec = solve_record(p.A, p.b, p.part, p.t, s)
+    key = f"{name}/t{p.t}/s{s}/{cfg['variant']}/sstep/fp64"
+    store(key, rec)
+    print(key, rec["iters"], rec["status"], f"{rec['seconds']:.1f}s", flush=True)
+
+
 def main(names):
     if names and names[0] == "--perturbed":
         perturbed(int(names[1]), names[2])
+        return
+    if names and names[0] == "--s":
+        one_s(int(names[1]), names[2])
+        return
+    if names == ["diff2d"]:
+        diff2d()
         return
     data = json.load(open(OUT)) if os.path.exists(OUT) else {}
     for name in names:

@@ -137,7 +137,8 @@ def ragged_problem(t=4):
 @pytest.mark.parametrize("variant,basis", [("sre", "sstep"), ("sre2", "sstep"),
                                            ("msdo", "sstep"), ("sre", "ca7"),
                                            ("sre2", "ca7"), ("msdo", "ca7"),
-                                           ("sre", "ca5"), ("msdo", "ca5")])
+                                           ("sre", "ca5"), ("sre2", "ca5"),
+                                           ("msdo", "ca5")])
 @pytest.mark.parametrize("s", [1, 2, 3])
 def test_solver_parity_ragged(variant, basis, s):
     A, b, part = ragged_problem()
@@ -229,6 +230,36 @@ def test_ani3d_small_parity(s):
     part = wl.partition_boxes((24, 24, 24), 32)
     b = wl.rhs_uniform(A.n, 1)
     check_parity(A, b, part, 32, s)
+
+
+@pytest.mark.parametrize("variant", ["sre", "sre2", "msdo"])
+def test_ca7_s8_t32_gram_256(variant):
+    """CA forms with the modified CA-Arnoldi (Algorithm 7) at s = 8, t = 32: every
+    iteration A-orthonormalises an n x 256 block V = [W, A W, ..., A^7 W], so the A-CholQR
+    Gram is 256 x 256 (the largest the library takes).  At s = 8 the power basis is
+    numerically rank deficient (Section 4: the CA forms lose stability as s grows); on the
+    Ani3D-like operator on 10^3 boxes the oracle's max|Q^T A Q - I| grows from 1e-5 to
+    3e-2 within three iterations and the Cholesky pivot test stops the solve.  The GPU must
+    stop the same way at the same iteration (within one), agree on the residual norms while
+    the basis is still A-orthonormal (iterations 1 and 2) and return the same last complete
+    iterate.  Tolerance 1e-4: the oracle's own basis is A-orthonormal only to 1e-5 - 7e-5 in
+    these iterations, and rounding differences in V^T A V enter the residual norms scaled
+    by that loss (two float64 implementations agree to a few 1e-6 here)."""
+    A = wl.stencil_matrix((10, 10, 10), aniso=(1.0, 1.0, 1e-3))
+    part = wl.partition_boxes((10, 10, 10), 32)
+    b = wl.rhs_uniform(A.n, 1)
+    ref = o.solve(A, b, part, 32, 8, tol=1e-8, maxit=100, variant=variant, basis="ca7")
+    assert ref.status == o.BREAKDOWN
+    S = ekcg.Solver(A, 32, part, variant=variant, basis="ca7", max_s=8,
+                    max_basis_bytes=1 << 30)
+    x, it, hist, st = S.solve(dev(b), s=8, tol=1e-8, maxit=100)
+    S.close()
+    assert st == ekcg.EKCG_EBREAKDOWN
+    assert abs(it - ref.iters) <= 1, (it, ref.iters)
+    np.testing.assert_allclose(hist[:3], ref.hist[:3], rtol=1e-4)
+    if it == ref.iters:
+        x = x.cpu().numpy()
+        assert np.linalg.norm(x - ref.x) <= 1e-4 * np.linalg.norm(ref.x)
 
 
 def test_sky3d_small_parity():
@@ -397,24 +428,19 @@ def test_ani3d_full_size_sampled():
 @pytest.mark.slow
 def test_sky3d_full_size_against_oracle_record():
     """Sky3D-like 96^3 (coefficient 1 / 1e3 on 8^3 blocks), t = 16, s = 4, float64: the
-    iteration count and the first 21 residual norms against the oracle's whole-solve
-    record (tests/golden/oracle_counts.json, written by the oracle only), and the true
-    relative residual.  s-step SRE-CG with s = 4 on this 1e3-contrast problem loses
-    A-orthogonality as the iteration proceeds, so its iteration count moves under
-    rounding-level changes; the record also holds the oracle's own counts with b perturbed
-    by 1e-15 (relative), and the GPU count must lie within that range widened by one."""
+    iteration count within one of the oracle's whole-solve record
+    (tests/golden/oracle_counts.json, written by the oracle only), the first 21 residual
+    norms to 1e-6 and the true relative residual."""
     import json
     gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden",
                                        "oracle_counts.json")))
     key = "sky3d/t16/s4/sre/sstep/fp64"
     g = gold[key]
-    counts = [g["iters"]] + [v["iters"] for k, v in gold.items()
-                             if k.startswith(key + "/perturbed/")]
     p = wl.sky3d(96, 16, seed=2)
     S = ekcg.Solver(p.A, 16, p.part, max_s=4)
     x, it, hist, st = S.solve(dev(p.b), s=4, tol=1e-8, maxit=5000)
     assert st == 0
-    assert min(counts) - 1 <= it <= max(counts) + 1, (it, counts)
+    assert abs(it - g["iters"]) <= 1, (it, g["iters"])
     np.testing.assert_allclose(hist[:21], g["hist"][:21], rtol=1e-6)
     assert relres(p.A, p.b, x.cpu().numpy()) <= 1e-8 * 1.01
     S.close()
