@@ -92,7 +92,7 @@ typedef struct {
 
 /* Fill *opts with the defaults: SRE, SSTEP, ACHOLQR, FP64, max_s 8, max_blocks 0,
  * max_basis_bytes 0, breakdown_tol 1e-14, inner_tol 1e-4, max_refine 30, profile 0,
- * contraction EKCG_CONTRACT_FP64.                                                         */
+ * contraction EKCG_CONTRACT_SPLIT.                                                        */
 void ekcg_default_opts(ekcg_opts* opts);
 
 /* Build a solver context for the SPD matrix A (Section 2) and its t-way partition.

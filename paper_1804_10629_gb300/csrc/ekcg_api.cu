@@ -1675,7 +1675,7 @@ void ekcg_default_opts(ekcg_opts* o) {
     o->inner_tol = 1e-4;
     o->max_refine = 30;
     o->profile = 0;
-    o->contraction = EKCG_CONTRACT_FP64;
+    o->contraction = EKCG_CONTRACT_SPLIT;
 }
 
 int ekcg_setup(int64_t n, const int64_t* rowptr, const int32_t* colind, const double* val,

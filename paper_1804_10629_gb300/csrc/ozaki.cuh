@@ -164,18 +164,25 @@ __device__ __forceinline__ uint32_t pack_bf16(uint32_t f0, uint32_t f1) {
 //   warps 0-7  (slicers): per 128-row tile, load the tile's X values (each thread half a row,
 //              P/2 values), take the row binade, and cut the values into the eight slices,
 //              one K-step (16 columns) at a time, into a ring of kStages shared stages;
-//   warp 8     (MMA): one thread issues the 36 pair MMAs of every K-step into one of two
-//              tensor-memory accumulator sets and commits each stage back to the slicers
+//   warp 8     (MMA): per K-step one thread issues one MMA per X slice a, against the C
+//              slices 1 .. 9 - a stacked along N (N = (9 - a) Q), starting at the columns of
+//              group a + 1, so every pair (a, b) accumulates into group a + b; one of two
+//              tensor-memory accumulator sets; each stage is committed back to the slicers
 //              and each finished tile to the epilogue;
 //   warps 9-12 (epilogue): lane quarter w % 4 reads its 32 rows of the finished set,
-//              combines the eight groups, applies scale and subtraction and writes OUT.
+//              combines the eight groups, applies scale and subtraction and writes OUT;
+//   warp 13    (prefetch): while the slicers start tile k it asks L2 for the X and Y rows
+//              of tile k + 2 (bulk prefetches), so the slicers' and the epilogue's loads
+//              find their rows in L2 and HBM streams without gaps.
 // mbarriers: full[s] / empty[s] per ring stage, acc_full[b] / acc_empty[b] and
 // erow_full[b] per accumulator set.  Each wait is bounded; a wait that runs out sets a
 // shared abort word that every role checks, so all roles leave their loops.
 constexpr int kSlicerWarps = 8;
 constexpr int kMmaWarp = 8;
 constexpr int kEpiWarp0 = 9;
-constexpr int kUpdThreads = 13 * 32;
+constexpr int kPrefetchWarp = 13;
+constexpr int kUpdThreads = 14 * 32;
+constexpr int kPrefetchAhead = 2;   // tiles of lead of the L2 prefetch
 constexpr int kKS = 16;          // columns of X per ring stage (one MMA K-step)
 constexpr int kStages = 4;
 
@@ -186,10 +193,12 @@ struct UpdShape {
     static constexpr int kSliceStage = kTile * kKS * 2;            // one slice of one stage
     static constexpr int kStageBytes = kSlices * kSliceStage;      // 32 KB
     static constexpr int kSliceB = Q * P * 2;                      // one slice of C
+    // the eight C slices are stacked along N (B row (b - 1) Q + q), so one MMA of N =
+    // (9 - a) Q per X slice a deposits every pair (a, b) into group a + b
     static constexpr int kOffB = kStages * kStageBytes;
     static constexpr int kSmem = kOffB + kSlices * kSliceB + 1024;  // + alignment slack
     static constexpr int kLboA = (kTile / 8) * 128;                // next 8 columns of A
-    static constexpr int kLboB = (Q / 8) * 128;                    // next 8 columns of B
+    static constexpr int kLboB = (kSlices * Q / 8) * 128;          // next 8 columns of B
     static constexpr uint32_t kAcc = (uint32_t)(kGroups * Q);      // columns of one set
     static constexpr uint32_t kCols = 2 * kAcc;                    // two sets
     static constexpr int kKSteps = P / kKS;
@@ -220,6 +229,40 @@ __device__ __forceinline__ bool bar_or(int id, int count, bool v) {
         : "memory");
     return r != 0;
 }
+// hint: bring [p, p + bytes) into L2 (p 16-byte aligned, bytes a multiple of 16)
+__device__ __forceinline__ void prefetch_l2(const void* p, uint32_t bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+// the rows [r0, r0 + rows) of every block of a multi-block operand, into L2
+__device__ __forceinline__ void prefetch_rows(const MB<const double>& M, int64_t r0, int64_t rows,
+                                              int64_t n) {
+    if (r0 >= n) return;
+    const int64_t cnt = (r0 + rows <= n ? rows : n - r0) * M.w;
+    for (int b = 0; b < M.count; ++b)
+        for (int64_t off = 0; off < cnt; off += 8192)   // pieces of at most 64 KB
+            prefetch_l2(M.blk(b) + r0 * M.w + off,
+                        (uint32_t)((cnt - off < 8192 ? cnt - off : 8192) * sizeof(double)));
+}
+// The prefetch role: `started` counts the tiles the slicers have begun; whenever it moves,
+// ask L2 for the rows of the tile kPrefetchAhead ahead of the newest one.  The prefetch is
+// only a hint, so a role that waits too long simply stops.
+template <typename F>
+__device__ __forceinline__ void prefetch_role(volatile int* started, volatile int* abort,
+                                              int my_tiles, int ahead, F issue) {
+    for (int d = 0; d < ahead && d < my_tiles; ++d) issue(d);
+    int done = 0;
+    long long t0 = clock64();
+    while (done < my_tiles && !*abort) {
+        const int st = *started;
+        if (st > done) {
+            done = st;
+            if (st - 1 + ahead < my_tiles) issue(st - 1 + ahead);
+            t0 = clock64();
+        } else if (clock64() - t0 > bulk::kWaitCycles) {
+            break;
+        }
+    }
+}
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bulk::smem_addr(bar))
                  : "memory");
@@ -243,6 +286,7 @@ k_oz_update(MB<const double> X, const double* __restrict__ C, MB<const double> Y
     __shared__ int erow[2][kTile];
     __shared__ int fcol[Q];
     __shared__ volatile int abort_flag;
+    __shared__ volatile int started;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t sA = bulk::smem_addr(sm), sB = sA + S::kOffB;
 
@@ -259,6 +303,7 @@ k_oz_update(MB<const double> X, const double* __restrict__ C, MB<const double> Y
         }
         bulk::mbar_init(&fin, 1);
         abort_flag = 0;
+        started = 0;
         bulk::fence_barrier_init();
     }
     // C: column binades, then the slices of every entry into the B operand (N = Q x K = P)
@@ -275,11 +320,14 @@ k_oz_update(MB<const double> X, const double* __restrict__ C, MB<const double> Y
         const bool neg = (__double_as_longlong(c) >> 63) != 0;
         const uint32_t ms = sign_magic(neg);
         const float undo = sign_undo(neg);
-        const int off = ((k >> 3) * (Q / 8) + (q >> 3)) * 128 + (q & 7) * 16 + (k & 7) * 2;
 #pragma unroll
-        for (int a = 0; a < kSlices; ++a)
-            *reinterpret_cast<uint16_t*>(sm + S::kOffB + a * S::kSliceB + off) =
+        for (int a = 0; a < kSlices; ++a) {
+            const int nrow = a * Q + q;
+            const int off = ((k >> 3) * (kSlices * Q / 8) + (nrow >> 3)) * 128 + (nrow & 7) * 16 +
+                            (k & 7) * 2;
+            *reinterpret_cast<uint16_t*>(sm + S::kOffB + off) =
                 (uint16_t)(slice_bits(F, a, ms, undo) >> 16);
+        }
     }
     fence_async_smem();
     tc_fence_before();
@@ -297,6 +345,7 @@ k_oz_update(MB<const double> X, const double* __restrict__ C, MB<const double> Y
             const int buf = lt & 1;
             if (lt >= 2 && !wait_or_abort(&acc_empty[buf], ((lt >> 1) - 1) & 1, &abort_flag))
                 break;
+            if (tid == 0) started = lt + 1;
             const int64_t i = tile * kTile + r;
             double xv[P / 2];
 #pragma unroll
@@ -363,7 +412,6 @@ k_oz_update(MB<const double> X, const double* __restrict__ C, MB<const double> Y
     } else if (warp == kMmaWarp) {
         // ---- MMA issue (one thread)
         if (lane == 0) {
-            constexpr uint32_t idesc = idesc_bf16_f32(kTile, Q);
             int stage = 0;
             int lt = 0;
             for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++lt) {
@@ -381,17 +429,16 @@ k_oz_update(MB<const double> X, const double* __restrict__ C, MB<const double> Y
                         break;
                     }
                     tc_fence_after();
-#pragma unroll 1
+                    const uint64_t bd = smem_desc(sB + j * 2 * S::kLboB, S::kLboB, 128);
+#pragma unroll
                     for (int a = 1; a <= kSlices; ++a) {
+                        // X slice a times C slices 1 .. 9 - a: pair (a, b) lands in the
+                        // columns of group a + b
                         const uint64_t ad = smem_desc(
                             sA + slot * S::kStageBytes + (a - 1) * S::kSliceStage, S::kLboA, 128);
-#pragma unroll 1
-                        for (int b = 1; b <= kGroups + 1 - a; ++b) {
-                            const uint64_t bd = smem_desc(
-                                sB + (b - 1) * S::kSliceB + j * 2 * S::kLboB, S::kLboB, 128);
-                            mma_bf16(dacc + (uint32_t)((a + b - 2) * Q), ad, bd, idesc,
-                                     (j > 0 || a > 1) ? 1u : 0u);
-                        }
+                        mma_bf16(dacc + (uint32_t)((a - 1) * Q), ad, bd,
+                                 idesc_bf16_f32(kTile, (kGroups + 1 - a) * Q),
+                                 (j > 0 || a > 1) ? 1u : 0u);
                     }
                     mma_commit(&empty[slot]);
                     ++stage;
@@ -402,6 +449,16 @@ k_oz_update(MB<const double> X, const double* __restrict__ C, MB<const double> Y
             // every MMA issued has completed before the tensor memory is released
             mma_commit(&fin);
             bulk::mbar_wait(&fin, 0);
+        }
+        __syncwarp();
+    } else if (warp == kPrefetchWarp) {
+        if (lane == 0) {
+            const int my_tiles = (int)((ntiles - blockIdx.x + gridDim.x - 1) / gridDim.x);
+            prefetch_role(&started, &abort_flag, my_tiles, kPrefetchAhead, [&](int lt) {
+                const int64_t r0 = (blockIdx.x + (int64_t)lt * gridDim.x) * kTile;
+                prefetch_rows(X, r0, kTile, n);
+                if (beta_on) prefetch_rows(Y, r0, kTile, n);
+            });
         }
         __syncwarp();
     } else {
@@ -425,8 +482,21 @@ k_oz_update(MB<const double> X, const double* __restrict__ C, MB<const double> Y
                     tmem_ld8(taddr + (uint32_t)(gi * Q + col0), g[gi]);
                 tmem_wait_ld();
                 if (ri < n) {
-                    const double* yr = beta_on ? Y.blk(0) + ri * Y.w + col0 : nullptr;
-                    double* orow = OUT.blk(0) + ri * OUT.w + col0;
+                    double yv[8];
+                    if (beta_on) {
+                        const double2* yr =
+                            reinterpret_cast<const double2*>(Y.blk(0) + ri * Y.w + col0);
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            const double2 v = yr[u];
+                            yv[2 * u] = v.x;
+                            yv[2 * u + 1] = v.y;
+                        }
+                    } else {
+#pragma unroll
+                        for (int u = 0; u < 8; ++u) yv[u] = 0.0;
+                    }
+                    double ov[8];
 #pragma unroll
                     for (int u = 0; u < 8; ++u) {
                         long long hi = 0, lo = 0;
@@ -442,9 +512,11 @@ k_oz_update(MB<const double> X, const double* __restrict__ C, MB<const double> Y
                             ex < 1 ? 0.0
                                    : (ex > 2046 ? __longlong_as_double(0x7FF0000000000000ll)
                                                 : __longlong_as_double((long long)ex << 52));
-                        orow[u] = fma((double)(beta_on ? -v7 : v7), scale,
-                                      beta_on ? yr[u] : 0.0);
+                        ov[u] = fma((double)(beta_on ? -v7 : v7), scale, yv[u]);
                     }
+                    double2* orow = reinterpret_cast<double2*>(OUT.blk(0) + ri * OUT.w + col0);
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) orow[u] = make_double2(ov[2 * u], ov[2 * u + 1]);
                 }
             }
             tc_fence_before();
@@ -472,11 +544,14 @@ k_oz_update(MB<const double> X, const double* __restrict__ C, MB<const double> Y
 //              warp = (column block, row parity); pass 1 takes the column binades of the
 //              tile (a shared max over the two row parities), pass 2 cuts 8 rows x 1 column
 //              per thread and K-step into the ring;
-//   warp 6     (MMA): 36 pair MMAs (M = 64, N = Q, K = 16) per K-step;
+//   warp 6     (MMA): per K-step one MMA per X slice a (M = 64, K = 16) against the Y
+//              slices 1 .. 9 - a stacked along N, into the columns of groups a + 1 .. 9;
+//   warp 7     (prefetch): asks L2 for the rows of tile k + 2 when the slicers start k;
 //   warps 8-11 (epilogue): M = 64 keeps rows 16 q' .. 16 q' + 15 of D in lanes 0-15 of lane
 //              quarter q', so lanes 0-15 of warp 8 + q' own the outputs p = 16 q' + lane.
 constexpr int kGramThreads = 12 * 32;
 constexpr int kGramMmaWarp = 6;
+constexpr int kGramPrefetchWarp = 7;
 constexpr int kGramEpiWarp0 = 8;
 constexpr int kGramRows = 128;       // rows per tile (binade scope, exact fp32 sums)
 constexpr int kGramStages = 6;
@@ -492,7 +567,7 @@ struct GramShape {
     static constexpr int kOffB = kSlices * kSliceA;                // B inside a stage
     static constexpr int kSmem = kGramStages * kStageBytes + 1024;
     static constexpr int kLboA = (kM / 8) * 128;
-    static constexpr int kLboB = (Q / 8) * 128;
+    static constexpr int kLboB = (kSlices * Q / 8) * 128;          // Y slices stacked in N
     static constexpr uint32_t kAcc = (uint32_t)(kGroups * Q);
     static constexpr uint32_t kCols = 2 * kAcc;
     static constexpr int kT = P + Q;                               // columns sliced per row
@@ -515,6 +590,7 @@ k_oz_gram(MB<const double> X, MB<const double> Y, int64_t n, double* __restrict_
     __shared__ int cexp[2][S::kT];          // tile binades: X columns, then Y columns
     __shared__ int cmax[2][S::kNB * 32];    // per row parity, pass 1
     __shared__ volatile int abort_flag;
+    __shared__ volatile int started;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t sbase = bulk::smem_addr(sm);
 
@@ -531,6 +607,7 @@ k_oz_gram(MB<const double> X, MB<const double> Y, int64_t n, double* __restrict_
         }
         bulk::mbar_init(&fin, 1);
         abort_flag = 0;
+        started = 0;
         bulk::fence_barrier_init();
     }
     // the ring starts zeroed: rows p >= P of the A operand stay zero
@@ -563,6 +640,7 @@ k_oz_gram(MB<const double> X, MB<const double> Y, int64_t n, double* __restrict_
                 !wait_or_abort(&acc_empty[buf], ((lt >> 1) - 1) & 1, &abort_flag))
                 failed = true;
             if (bar_or(1, S::kSlicers * 32, failed || abort_flag)) break;
+            if (tid == 0) started = lt + 1;
             const int64_t r0 = tile * kGramRows;
             // pass 1: binade of the column over the tile (this parity's row groups)
             int e = 0;
@@ -604,12 +682,13 @@ k_oz_gram(MB<const double> X, MB<const double> Y, int64_t n, double* __restrict_
                         ms[u] = sign_magic(neg);
                         undo[u] = sign_undo(neg);
                     }
+                    // X: slice a at a * kSliceA; Y: slice a is B rows a Q .. a Q + Q - 1
                     unsigned char* dst =
                         sm + slot * S::kStageBytes +
                         (isx ? (par * (S::kM / 8) + (cc >> 3)) * 128
-                             : S::kOffB + (par * (Q / 8) + (cc >> 3)) * 128) +
+                             : S::kOffB + (par * (kSlices * Q / 8) + (cc >> 3)) * 128) +
                         (cc & 7) * 16;
-                    const int sstride = isx ? S::kSliceA : S::kSliceB;
+                    const int sstride = isx ? S::kSliceA : (Q / 8) * 128;
 #pragma unroll
                     for (int a = 0; a < kSlices; ++a) {
                         uint4 v;
@@ -631,7 +710,6 @@ k_oz_gram(MB<const double> X, MB<const double> Y, int64_t n, double* __restrict_
         }
     } else if (warp == kGramMmaWarp) {
         if (lane == 0) {
-            constexpr uint32_t idesc = idesc_bf16_f32(S::kM, Q);
             int stage = 0;
             int lt = 0;
             for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++lt) {
@@ -650,16 +728,13 @@ k_oz_gram(MB<const double> X, MB<const double> Y, int64_t n, double* __restrict_
                     }
                     tc_fence_after();
                     const uint32_t st = sbase + slot * S::kStageBytes;
-#pragma unroll 1
+                    const uint64_t bd = smem_desc(st + S::kOffB, S::kLboB, 128);
+#pragma unroll
                     for (int a = 1; a <= kSlices; ++a) {
                         const uint64_t ad = smem_desc(st + (a - 1) * S::kSliceA, S::kLboA, 128);
-#pragma unroll 1
-                        for (int b = 1; b <= kGroups + 1 - a; ++b) {
-                            const uint64_t bd = smem_desc(
-                                st + S::kOffB + (b - 1) * S::kSliceB, S::kLboB, 128);
-                            mma_bf16(dacc + (uint32_t)((a + b - 2) * Q), ad, bd, idesc,
-                                     (ks > 0 || a > 1) ? 1u : 0u);
-                        }
+                        mma_bf16(dacc + (uint32_t)((a - 1) * Q), ad, bd,
+                                 idesc_bf16_f32(S::kM, (kGroups + 1 - a) * Q),
+                                 (ks > 0 || a > 1) ? 1u : 0u);
                     }
                     mma_commit(&empty[slot]);
                     ++stage;
@@ -669,6 +744,16 @@ k_oz_gram(MB<const double> X, MB<const double> Y, int64_t n, double* __restrict_
             }
             mma_commit(&fin);
             bulk::mbar_wait(&fin, 0);
+        }
+        __syncwarp();
+    } else if (warp == kGramPrefetchWarp) {
+        if (lane == 0) {
+            const int my_tiles = (int)((ntiles - blockIdx.x + gridDim.x - 1) / gridDim.x);
+            prefetch_role(&started, &abort_flag, my_tiles, kPrefetchAhead, [&](int lt) {
+                const int64_t r0 = (blockIdx.x + (int64_t)lt * gridDim.x) * kGramRows;
+                prefetch_rows(X, r0, kGramRows, n);
+                prefetch_rows(Y, r0, kGramRows, n);
+            });
         }
         __syncwarp();
     } else if (warp >= kGramEpiWarp0) {

@@ -334,7 +334,7 @@ class Solver:
     def __init__(self, A, t, part, variant="sre", basis="sstep", orth="acholqr",
                  precision="fp64", max_s=8, max_blocks=0, max_basis_bytes=0,
                  breakdown_tol=1e-14, inner_tol=1e-4, max_refine=30, profile=False,
-                 stream=None, contraction="fp64"):
+                 stream=None, contraction=None):
         import torch
         o = ekcg_default_opts()
         o.variant, o.basis, o.orth = VARIANT[variant], BASIS[basis], ORTH[orth]
@@ -342,7 +342,8 @@ class Solver:
         o.max_s, o.max_blocks, o.max_basis_bytes = max_s, max_blocks, max_basis_bytes
         o.breakdown_tol, o.inner_tol, o.max_refine = breakdown_tol, inner_tol, max_refine
         o.profile = int(bool(profile))
-        o.contraction = CONTRACTION[contraction]
+        if contraction is not None:          # None: the library default (split products)
+            o.contraction = CONTRACTION[contraction]
         if stream is None:
             stream = torch.cuda.current_stream().cuda_stream
         self.n = int(A.n)
