@@ -26,9 +26,9 @@ sys.path.insert(0, ROOT)
 
 import workloads as wl  # noqa: E402
 
-# FP64 ALU peak of one GB300: 152 SMs x 2 FP64 FMA per clock per SM x 2 flop x 2.07 GHz
-# (unit count inferred from a measured 1.20 TFLOP/s DFMA loop; the nominal figure is 1.25).
-FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+# FP32 ALU peak: SMs x 128 FMA per clock x 2 flop x 2.07 GHz (the SM count is read from the
+# device at run time; 152 on GB300).  The FP64 FMA peak is measured live by the library's
+# ekcg_fp64_fma_rate (a DFMA loop over every SM).
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 HBM_FALLBACK_GBS = 6800.0
 
@@ -55,6 +55,9 @@ def parse():
     ap.add_argument("--variant", default="")
     ap.add_argument("--basis", default="sstep")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32_ir"])
+    ap.add_argument("--contraction", default="split", choices=["split", "fp64"],
+                    help="float64 CGS / Gram contractions: tensor-core split products "
+                         "(default) or float64 FMAs")
     ap.add_argument("--precond", default=None, choices=["ic0"],
                     help="block Jacobi split preconditioning, IC(0) blocks on 64 boxes")
     ap.add_argument("--sweep", action="store_true",
@@ -138,23 +141,27 @@ def measured_traffic(kernel_class):
         return None
 
 
-def roofline_and_table(prof, args):
+def roofline_and_table(prof, args, fp64_peak=None):
     """Roofline of the dominant kernel class (by device time) and the per-class table.
-    float64: FP64 ALU bound (alu) for the arithmetic kernels; otherwise the HBM bound."""
+    float64 with float64-FMA contractions: FP64 ALU bound (alu, against the measured FMA
+    rate) for the arithmetic kernels; the split-product Gram and update classes and every
+    float32 kernel: the HBM bound on algorithmic bytes."""
     pk = peaks()
     hbm = pk.get("hbm_gbs")
     roof = None
+    alu64 = ("spmm", "chol_inv", "xr_update", "gram_reduce", "trsm")
+    if args.contraction == "fp64":
+        alu64 = alu64 + ("gram", "block_update")
     if prof:
         name, d = max(prof.items(), key=lambda kv: kv[1]["ms"])
         sec = d["ms"] / 1e3
-        if args.precision == "fp64" and name in ("gram", "block_update", "spmm", "chol_inv",
-                                                   "xr_update", "gram_reduce"):
+        ratio = measured_traffic(name)
+        traffic = (ratio * d["bytes"] / max(d["launches"], 1)) if ratio else None
+        if args.precision == "fp64" and name in alu64 and fp64_peak:
             ach = d["flops"] / sec / 1e12
-            ratio = measured_traffic(name)
-            traffic = (ratio * d["bytes"] / max(d["launches"], 1)) if ratio else None
             roof = {"kernel": name, "bound": "alu", "achieved": ach,
-                    "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS,
-                    "peak_source": "derived FP64 FMA rate: 152 SMs x 2 DFMA/clk x 2 x 2.07 GHz",
+                    "peak": fp64_peak, "unit": "TFLOP/s", "frac": ach / fp64_peak,
+                    "peak_source": "measured FP64 FMA rate (ekcg_fp64_fma_rate, this run)",
                     "traffic": traffic, "algorithmic_bytes_per_launch":
                         d["bytes"] / max(d["launches"], 1),
                     "launches": d["launches"], "avg_launch_ms": d["ms"] / max(d["launches"], 1)}
@@ -172,7 +179,9 @@ def roofline_and_table(prof, args):
             roof = {"kernel": name, "bound": "hbm", "achieved": ach, "peak": peak,
                     "unit": "GB/s", "frac": ach / peak,
                     "peak_source": "of measured" if hbm else "of fallback",
-                    "traffic": None, "launches": d["launches"],
+                    "traffic": traffic, "algorithmic_bytes_per_launch":
+                        d["bytes"] / max(d["launches"], 1),
+                    "launches": d["launches"],
                     "avg_launch_ms": d["ms"] / max(d["launches"], 1)}
     table = {k: {"ms_per_step": v["ms"] / args.steps,
                  "launches_per_step": v["launches"] / args.steps,
@@ -505,10 +514,12 @@ def main():
     variant = args.variant or cfg["variant"]
     stream = torch.cuda.Stream()
     t0 = time.perf_counter()
+    sm_count, fp64_peak = ekcg.ekcg_fp64_fma_rate(stream.cuda_stream)
     with torch.cuda.stream(stream):
         S = ekcg.Solver(prob.A, prob.t, prob.part, variant=variant, basis=args.basis,
                         precision=args.precision, max_s=s, profile=True,
-                        stream=stream.cuda_stream, max_basis_bytes=64 << 30)
+                        stream=stream.cuda_stream, max_basis_bytes=64 << 30,
+                        contraction=args.contraction)
     if args.precond:
         # block Jacobi over 64 geometric boxes (the paper's 64 subdomains), each inside one
         # of the workload's t domains
@@ -553,7 +564,7 @@ def main():
                  "x_rel_diff_vs_fp64": float(np.linalg.norm(xmh - xs) / np.linalg.norm(xs))}
         M.close()
 
-    roof, kernel_table = roofline_and_table(prof, args)
+    roof, kernel_table = roofline_and_table(prof, args, fp64_peak)
 
     # end to end through the host-buffer C-ABI call (H2D of b and D2H of x inside)
     e2e = None
@@ -585,6 +596,9 @@ def main():
             "data": "synthetic",
             "config": {"workload": f"{prob.name} n={prob.A.n} nnz={prob.A.nnz} t={prob.t} "
                                    f"s={s} {variant} {args.basis} {args.precision}",
+                       "contraction": ("tensor-core split products (float64-accurate)"
+                                       if args.contraction == "split" else "float64 FMA"),
+                       "sm_count": sm_count, "fp64_fma_tflops_measured": fp64_peak,
                        "desc": cfg["desc"], "tol": args.tol, "iters": its,
                        "true_relres": relres, "status": st,
                        "l2": "working set larger than L2 (matrix + n x t blocks)",

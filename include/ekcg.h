@@ -182,6 +182,14 @@ int ekcg_block_ic0_host(int64_t n, const int64_t* rowptr, const int32_t* colind,
  * stays usable afterwards.  Allocates and frees one int.                                 */
 int ekcg_wait_selftest(long long limit_cycles, void* stream);
 
+/* Measurement, no counterpart in the paper: the float64 FMA rate of the current device
+ * (every thread of 8 CTAs per SM x 256 threads runs 16 independent fused multiply-add
+ * chains; timed with CUDA events on `stream`, after a warm-up launch).  *num_sms receives
+ * the device's SM count, *tflops 2 x FMAs per second / 1e12: the roofline peak of the
+ * float64-FMA kernels.  Allocates and frees one double.  Errors: EKCG_EINVAL (NULL
+ * outputs), EKCG_ENOMEM, EKCG_ECUDA.                                                      */
+int ekcg_fp64_fma_rate(void* stream, int* num_sms, double* tflops);
+
 /* Turn the per-launch CUDA-event timing of later solves on (on != 0) or off, whatever
  * opts.profile was at setup.  Errors: EKCG_EINVAL (NULL ctx).                            */
 int ekcg_set_profile(ekcg_ctx* ctx, int on);

@@ -1943,6 +1943,49 @@ int ekcg_wait_selftest(long long limit_cycles, void* stream) {
     return (h & 4) ? EKCG_ETIMEOUT : EKCG_OK;
 }
 
+// Measured float64 FMA rate of the device: every thread runs 16 independent FMA chains.
+__global__ void k_fp64_fma_rate(double* out, int iters, double a, double b) {
+    double x[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) x[i] = threadIdx.x + i;
+    for (int k = 0; k < iters; ++k)
+#pragma unroll
+        for (int i = 0; i < 16; ++i) x[i] = fma(x[i], a, b);
+    double s = 0.0;
+#pragma unroll
+    for (int i = 0; i < 16; ++i) s += x[i];
+    if (s == 1.2345) out[0] = s;   // keeps the chains live; never true for these inputs
+}
+
+int ekcg_fp64_fma_rate(void* stream, int* num_sms, double* tflops) {
+    if (!num_sms || !tflops) return EKCG_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return EKCG_ECUDA;
+    double* d = nullptr;
+    if (cudaMalloc(&d, sizeof(double)) != cudaSuccess) return EKCG_ENOMEM;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const int blocks = sms * 8, threads = 256, iters = 1 << 14;
+    k_fp64_fma_rate<<<blocks, threads, 0, st>>>(d, 256, 0.999, 1e-3);   // warm-up
+    cudaEventRecord(e0, st);
+    k_fp64_fma_rate<<<blocks, threads, 0, st>>>(d, iters, 0.999, 1e-3);
+    cudaEventRecord(e1, st);
+    cudaError_t e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(d);
+    if (e != cudaSuccess || ms <= 0.f) return EKCG_ECUDA;
+    *num_sms = sms;
+    *tflops = 2.0 * (double)blocks * threads * 16.0 * iters / (ms * 1e-3) / 1e12;
+    return EKCG_OK;
+}
+
 int ekcg_set_profile(ekcg_ctx* c, int on) {
     if (!c) return EKCG_EINVAL;
     c->opts.profile = on ? 1 : 0;

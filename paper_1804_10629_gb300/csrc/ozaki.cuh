@@ -535,26 +535,28 @@ k_oz_update(MB<const double> X, const double* __restrict__ C, MB<const double> Y
 // ---- the Gram product ---------------------------------------------------------------
 // C = X^T Y over the n rows (CGS coefficients Q^T (A W), the A-CholQR Gram W^T (A W)):
 // X n x P (P <= 64, padded to the MMA's M = 64), Y n x Q (Q = 16 or 32).  The contraction
-// runs over rows, in tiles of 128 rows: every column of X and of Y is scaled by its binade
-// over the tile (e_p, f_q), so a tile's eight groups are exact in fp32 (<= 8 pairs x 128
-// rows x 127^2 < 2^24), and the epilogue adds the tile's V 2^{e_p + f_q - 2100} into a
+// runs over rows, in tiles of 64 rows: every column of X and of Y is scaled by its binade
+// over the tile (e_p, f_q), so a tile's eight groups are exact in fp32 (<= 8 pairs x 64
+// rows x 127^2 < 2^23), and the epilogue adds the tile's V 2^{e_p + f_q - 2100} into a
 // float64 accumulator per output held in registers across the CTA's tiles.  Each CTA writes
 // its P x Q partial sum; k_gram_reduce adds the partials in CTA order.
+//   warp 7     (producer): one thread copies the tile's rows of every X block and of Y
+//              (contiguous runs of 64 x w doubles) into one of two raw shared buffers with
+//              bulk copies completing on an mbarrier, one tile ahead of the slicers;
 //   warps 0 .. 2 nb - 1 (slicers, nb = ceil((P + Q) / 32) column blocks): lane = column,
 //              warp = (column block, row parity); pass 1 takes the column binades of the
-//              tile (a shared max over the two row parities), pass 2 cuts 8 rows x 1 column
-//              per thread and K-step into the ring;
+//              tile from the raw buffer (a shared max over the two row parities), pass 2
+//              cuts 8 rows x 1 column per thread and K-step into the stage ring;
 //   warp 6     (MMA): per K-step one MMA per X slice a (M = 64, K = 16) against the Y
 //              slices 1 .. 9 - a stacked along N, into the columns of groups a + 1 .. 9;
-//   warp 7     (prefetch): asks L2 for the rows of tile k + 2 when the slicers start k;
 //   warps 8-11 (epilogue): M = 64 keeps rows 16 q' .. 16 q' + 15 of D in lanes 0-15 of lane
 //              quarter q', so lanes 0-15 of warp 8 + q' own the outputs p = 16 q' + lane.
 constexpr int kGramThreads = 12 * 32;
 constexpr int kGramMmaWarp = 6;
-constexpr int kGramPrefetchWarp = 7;
+constexpr int kGramProducerWarp = 7;
 constexpr int kGramEpiWarp0 = 8;
-constexpr int kGramRows = 128;       // rows per tile (binade scope, exact fp32 sums)
-constexpr int kGramStages = 6;
+constexpr int kGramRows = 64;        // rows per tile (binade scope, exact fp32 sums)
+constexpr int kGramStages = 4;
 
 template <int P, int Q>
 struct GramShape {
@@ -565,7 +567,10 @@ struct GramShape {
     static constexpr int kSliceB = Q * kKS * 2;
     static constexpr int kStageBytes = kSlices * (kSliceA + kSliceB);
     static constexpr int kOffB = kSlices * kSliceA;                // B inside a stage
-    static constexpr int kSmem = kGramStages * kStageBytes + 1024;
+    static constexpr int kRawX = kGramRows * P * 8;                // raw X tile, bytes
+    static constexpr int kRawY = kGramRows * Q * 8;
+    static constexpr int kOffRaw = kGramStages * kStageBytes;      // raw buffers after ring
+    static constexpr int kSmem = kOffRaw + 2 * (kRawX + kRawY) + 1024;
     static constexpr int kLboA = (kM / 8) * 128;
     static constexpr int kLboB = (kSlices * Q / 8) * 128;          // Y slices stacked in N
     static constexpr uint32_t kAcc = (uint32_t)(kGroups * Q);
@@ -573,7 +578,7 @@ struct GramShape {
     static constexpr int kT = P + Q;                               // columns sliced per row
     static constexpr int kNB = (kT + 31) / 32;                     // column blocks
     static constexpr int kSlicers = 2 * kNB;                       // slicer warps (<= 6)
-    static constexpr int kKSteps = kGramRows / kKS;                // 8
+    static constexpr int kKSteps = kGramRows / kKS;                // 4
 };
 
 // partials[cta * 4096 + p * Q + q] = this CTA's share of (X^T Y)[p, q]
@@ -586,13 +591,17 @@ k_oz_gram(MB<const double> X, MB<const double> Y, int64_t n, double* __restrict_
     unsigned char* sm = oz_raw + ((1024 - (bulk::smem_addr(oz_raw) & 1023)) & 1023);
     __shared__ __align__(8) uint64_t full[kGramStages], empty[kGramStages];
     __shared__ __align__(8) uint64_t acc_full[2], acc_empty[2], cexp_full[2], fin;
+    __shared__ __align__(8) uint64_t raw_full[2], raw_empty[2];
     __shared__ uint32_t tslot;
     __shared__ int cexp[2][S::kT];          // tile binades: X columns, then Y columns
     __shared__ int cmax[2][S::kNB * 32];    // per row parity, pass 1
     __shared__ volatile int abort_flag;
-    __shared__ volatile int started;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t sbase = bulk::smem_addr(sm);
+    double* rawx[2] = {reinterpret_cast<double*>(sm + S::kOffRaw),
+                       reinterpret_cast<double*>(sm + S::kOffRaw + S::kRawX)};
+    double* rawy[2] = {reinterpret_cast<double*>(sm + S::kOffRaw + 2 * S::kRawX),
+                       reinterpret_cast<double*>(sm + S::kOffRaw + 2 * S::kRawX + S::kRawY)};
 
     if (warp == 0) tmem_alloc(&tslot, S::kCols);
     if (tid == 0) {
@@ -604,10 +613,11 @@ k_oz_gram(MB<const double> X, MB<const double> Y, int64_t n, double* __restrict_
             bulk::mbar_init(&acc_full[b], 1);
             bulk::mbar_init(&acc_empty[b], 4);
             bulk::mbar_init(&cexp_full[b], S::kSlicers);
+            bulk::mbar_init(&raw_full[b], 1);
+            bulk::mbar_init(&raw_empty[b], S::kSlicers);
         }
         bulk::mbar_init(&fin, 1);
         abort_flag = 0;
-        started = 0;
         bulk::fence_barrier_init();
     }
     // the ring starts zeroed: rows p >= P of the A operand stay zero
@@ -627,10 +637,11 @@ k_oz_gram(MB<const double> X, MB<const double> Y, int64_t n, double* __restrict_
         const bool active = c < S::kT;
         const bool isx = c < P;
         const int cc = isx ? c : c - P;                   // column inside X or Y
-        const MB<const double>& M = isx ? X : Y;
-        const int blk = active ? cc / M.w : 0, cw = active ? cc - blk * M.w : 0;
-        const double* base = M.blk(blk) + cw;
-        const int64_t ld = M.w;
+        const int w = isx ? X.w : Q;
+        const int blk = (active && isx) ? cc / X.w : 0;
+        const int cw = active ? cc - blk * w : 0;
+        // raw element (row, column) = raw[blk * 64 * w + row * w + cw]
+        const int raw_off = blk * kGramRows * w + cw;
         int stage = 0;
         int lt = 0;
         bool failed = false;   // the slicer warps leave together (they share named barriers)
@@ -639,19 +650,20 @@ k_oz_gram(MB<const double> X, MB<const double> Y, int64_t n, double* __restrict_
             if (lt >= 2 && !failed &&
                 !wait_or_abort(&acc_empty[buf], ((lt >> 1) - 1) & 1, &abort_flag))
                 failed = true;
+            if (!failed && !wait_or_abort(&raw_full[buf], (lt >> 1) & 1, &abort_flag))
+                failed = true;
             if (bar_or(1, S::kSlicers * 32, failed || abort_flag)) break;
-            if (tid == 0) started = lt + 1;
             const int64_t r0 = tile * kGramRows;
+            const int rows = (int)((n - r0) < kGramRows ? (n - r0) : kGramRows);
+            const double* raw = (isx ? rawx[buf] : rawy[buf]) + raw_off;
             // pass 1: binade of the column over the tile (this parity's row groups)
             int e = 0;
             if (active) {
-                for (int rg = par; rg < kGramRows / 8; rg += 2) {
 #pragma unroll
-                    for (int u = 0; u < 8; ++u) {
-                        const int64_t row = r0 + rg * 8 + u;
-                        if (row < n) e = max(e, bexp(base[row * ld]));
-                    }
-                }
+                for (int rg = par; rg < kGramRows / 8; rg += 2)
+#pragma unroll
+                    for (int u = 0; u < 8; ++u)
+                        if (rg * 8 + u < rows) e = max(e, bexp(raw[(rg * 8 + u) * w]));
             }
             cmax[par][cb * 32 + lane] = e;
             asm volatile("bar.sync 1, %0;" ::"r"(S::kSlicers * 32) : "memory");
@@ -670,13 +682,13 @@ k_oz_gram(MB<const double> X, MB<const double> Y, int64_t n, double* __restrict_
                     continue;
                 }
                 if (active) {
-                    const int64_t rowb = r0 + (2 * ks + par) * 8;
+                    const int rb = (2 * ks + par) * 8;
                     uint64_t F[8];
                     uint32_t ms[8];
                     float undo[8];
 #pragma unroll
                     for (int u = 0; u < 8; ++u) {
-                        const double x = (rowb + u < n) ? base[(rowb + u) * ld] : 0.0;
+                        const double x = (rb + u < rows) ? raw[(rb + u) * w] : 0.0;
                         F[u] = fixed56(x, e);
                         const bool neg = (__double_as_longlong(x) >> 63) != 0;
                         ms[u] = sign_magic(neg);
@@ -707,7 +719,30 @@ k_oz_gram(MB<const double> X, MB<const double> Y, int64_t n, double* __restrict_
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&full[slot]);
             }
+            // the raw buffer may be refilled
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&raw_empty[buf]);
         }
+    } else if (warp == kGramProducerWarp) {
+        if (lane == 0) {
+            int lt = 0;
+            for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++lt) {
+                const int buf = lt & 1;
+                if (lt >= 2 && !wait_or_abort(&raw_empty[buf], ((lt >> 1) - 1) & 1, &abort_flag))
+                    break;
+                const int64_t r0 = tile * kGramRows;
+                const int rows = (int)((n - r0) < kGramRows ? (n - r0) : kGramRows);
+                const uint32_t bx = (uint32_t)rows * X.w * 8, by = (uint32_t)rows * Q * 8;
+                bulk::mbar_expect_tx(&raw_full[buf], bx * X.count + by);
+                for (int b = 0; b < X.count; ++b)
+                    bulk::bulk_g2s(rawx[buf] + b * kGramRows * X.w, X.blk(b) + r0 * X.w, bx,
+                                   &raw_full[buf]);
+                bulk::bulk_g2s(rawy[buf], Y.blk(0) + r0 * Q, by, &raw_full[buf]);
+            }
+            // every copy issued has landed before the CTA exits
+            if (lt > 0) bulk::mbar_wait(&raw_full[(lt - 1) & 1], ((lt - 1) >> 1) & 1);
+        }
+        __syncwarp();
     } else if (warp == kGramMmaWarp) {
         if (lane == 0) {
             int stage = 0;
@@ -744,16 +779,6 @@ k_oz_gram(MB<const double> X, MB<const double> Y, int64_t n, double* __restrict_
             }
             mma_commit(&fin);
             bulk::mbar_wait(&fin, 0);
-        }
-        __syncwarp();
-    } else if (warp == kGramPrefetchWarp) {
-        if (lane == 0) {
-            const int my_tiles = (int)((ntiles - blockIdx.x + gridDim.x - 1) / gridDim.x);
-            prefetch_role(&started, &abort_flag, my_tiles, kPrefetchAhead, [&](int lt) {
-                const int64_t r0 = (blockIdx.x + (int64_t)lt * gridDim.x) * kGramRows;
-                prefetch_rows(X, r0, kGramRows, n);
-                prefetch_rows(Y, r0, kGramRows, n);
-            });
         }
         __syncwarp();
     } else if (warp >= kGramEpiWarp0) {

@@ -75,6 +75,8 @@ def _declare(L):
     L.ekcg_set_block_jacobi.restype = c_int
     L.ekcg_wait_selftest.argtypes = [c_longlong, c_void_p]
     L.ekcg_wait_selftest.restype = c_int
+    L.ekcg_fp64_fma_rate.argtypes = [c_void_p, POINTER(c_int), POINTER(c_double)]
+    L.ekcg_fp64_fma_rate.restype = c_int
     L.ekcg_set_profile.argtypes = [c_void_p, c_int]
     L.ekcg_set_profile.restype = c_int
     L.ekcg_profile.argtypes = [c_void_p, c_int, POINTER(c_char_p), POINTER(c_double),
@@ -248,6 +250,14 @@ def ekcg_block_ic0_host(A, bpart):
 def ekcg_wait_selftest(limit_cycles, stream=None):
     """Status of the bounded-wait diagnostic (EKCG_ETIMEOUT when the wait ran out)."""
     return lib().ekcg_wait_selftest(int(limit_cycles), c_void_p(stream))
+
+
+def ekcg_fp64_fma_rate(stream=None):
+    """(SM count, measured float64 FMA rate in TFLOP/s) of the current device."""
+    sms, tf = c_int(), c_double()
+    _check(lib().ekcg_fp64_fma_rate(c_void_p(stream) if stream else None, byref(sms),
+                                    byref(tf)), "ekcg_fp64_fma_rate")
+    return sms.value, tf.value
 
 
 def ekcg_profile(ctx, cap=32):
