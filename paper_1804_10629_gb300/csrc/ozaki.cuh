@@ -6,20 +6,20 @@
 // roofline.  Here it runs as a split ("Ozaki") product on the bf16 tensor cores:
 //
 //   * each row i of X (P values) is scaled by its largest binade, 2^{e_i - 1022}, and its
-//     magnitudes cut into a 56-bit fixed-point integer F = sum_a x_a 2^{56-7a}, eight 7-bit
+//     magnitudes cut into a 63-bit fixed-point integer F = sum_a x_a 2^{63-7a}, nine 7-bit
 //     slices x_a in [0, 127] carrying the sign of the value (exact in bf16);
 //   * each column q of C is cut the same way against its own binade 2^{f_q - 1022};
-//   * the slice products are integers below 2^14, so over K = P <= 64 terms and up to eight
+//   * the slice products are integers below 2^14, so over K = P <= 64 terms and up to nine
 //     slice pairs (a, b) with a + b = g the fp32 accumulator of tcgen05.mma holds the exact
-//     group sum G_g = sum_{a+b=g} sum_k x_a[i,k] c_b[k,q] (|G_g| < 2^23);
-//   * the 36 pairs with a + b <= 9 form eight groups g = 2..9, each in its own TMEM
+//     group sum G_g = sum_{a+b=g} sum_k x_a[i,k] c_b[k,q] (|G_g| < 2^24);
+//   * the 45 pairs with a + b <= 10 form nine groups g = 2..10, each in its own TMEM
 //     accumulator (128 lanes = rows, Q columns); the dropped pairs and the truncation of F
-//     weigh at most about 2^-52 of max|X_i| max|C_q| per term, the size of one float64
-//     rounding of that term;
-//   * the epilogue combines the eight exact groups in 64-bit integers,
-//     V = sum_g G_g 2^{7(9-g)} (kept as V >> 7 below 2^62), converts V once to float64 and
+//     weigh at most about 2^-60 of max|X_i| max|C_q| per term, below one float64 rounding of
+//     every term within 2^7 of that product;
+//   * the epilogue combines the nine exact groups in 64-bit integers,
+//     V = sum_g G_g 2^{7(10-g)} (kept as V >> 14 below 2^62), converts V once to float64 and
 //     applies the scale and the subtraction with one fused multiply-add:
-//     OUT = Y - V 2^{e_i + f_q - 2100}.
+//     OUT = Y - (V >> 14) 2^{e_i + f_q - 2100}.
 //
 // Tensor-core mechanics: A (X slices, 128 rows x K) and B (C slices, Q x K) sit in shared
 // memory in the canonical K-major no-swizzle layout of 8 x 16-byte core matrices (leading
@@ -41,8 +41,9 @@ namespace oz {
 
 constexpr int kThreads = 256;
 constexpr int kTile = 128;      // rows of X per tile (M of one MMA)
-constexpr int kSlices = 8;      // 7-bit slices of the 56-bit fixed-point magnitude
-constexpr int kGroups = 8;      // slice-pair groups g = a + b = 2..9
+constexpr int kSlices = 9;      // 7-bit slices of the 63-bit fixed-point magnitude
+constexpr int kGroups = 9;      // slice-pair groups g = a + b = 2..10
+constexpr int kMaxN = 256;      // largest N of one tcgen05.mma (M = 64 or 128)
 constexpr int kKC = 32;         // columns of X sliced per stage (K per stage)
 
 // ---- tcgen05 / descriptor helpers ------------------------------------------------------
@@ -108,8 +109,35 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
 #pragma unroll
     for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
 }
+// 32 lanes x 4 consecutive 32-bit columns
+__device__ __forceinline__ void tmem_ld4(uint32_t taddr, float (&v)[4]) {
+    uint32_t r[4];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(taddr)
+                 : "memory");
+#pragma unroll
+    for (int i = 0; i < 4; ++i) v[i] = __uint_as_float(r[i]);
+}
 __device__ __forceinline__ void tmem_wait_ld() {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// the nine exact group sums G_2 .. G_10 combined into V >> 14 with V = sum_g G_g 2^{7(10-g)}
+// (|G_g| < 2^24: hi = G_2..G_5 below 2^41, lo = G_6..G_10 below 2^52, the result below 2^62)
+__device__ __forceinline__ long long combine_groups(const float (&g)[kGroups]) {
+    long long hi = 0, lo = 0;
+#pragma unroll
+    for (int gi = 0; gi < 4; ++gi) hi = hi * 128 + (long long)__float2int_rn(g[gi]);
+#pragma unroll
+    for (int gi = 4; gi < kGroups; ++gi) lo = lo * 128 + (long long)__float2int_rn(g[gi]);
+    return hi * (1ll << 21) + (lo >> 14);
+}
+// 2^{ex - 1023} for a biased exponent ex: 0 below the normal range, infinity above it
+__device__ __forceinline__ double pow2_biased(int ex) {
+    return ex < 1 ? 0.0
+                  : (ex > 2046 ? __longlong_as_double(0x7FF0000000000000ll)
+                               : __longlong_as_double((long long)ex << 52));
 }
 
 // ---- slicing ----------------------------------------------------------------------------
@@ -117,14 +145,14 @@ __device__ __forceinline__ void tmem_wait_ld() {
 __device__ __forceinline__ int bexp(double x) {
     return (int)((__double_as_longlong(x) >> 52) & 0x7FF);
 }
-// 56-bit fixed-point magnitude of x against the binade 2^{e - 1022} (e >= bexp(x)):
-// floor(|x| 2^{56 - (e - 1022)}), below 2^56.
-__device__ __forceinline__ uint64_t fixed56(double x, int e) {
+// 63-bit fixed-point magnitude of x against the binade 2^{e - 1022} (e >= bexp(x)):
+// floor(|x| 2^{63 - (e - 1022)}), below 2^63.
+__device__ __forceinline__ uint64_t fixed63(double x, int e) {
     const uint64_t u = (uint64_t)__double_as_longlong(x);
     const int ex = (int)((u >> 52) & 0x7FF);
     if (ex == 0) return 0;
     const uint64_t m = (u & 0xFFFFFFFFFFFFFull) | (1ull << 52);
-    const int sh = ex - e + 3;   // <= 3
+    const int sh = ex - e + 10;   // <= 10
     if (sh >= 0) return m << sh;
     return (sh > -64) ? (m >> (-sh)) : 0;
 }
@@ -134,18 +162,19 @@ __device__ __forceinline__ uint32_t slice_f32_bits(uint32_t s7, uint32_t magic_s
                                                    float undo) {
     return __float_as_uint(__uint_as_float((s7 & 127u) | magic_sign) + undo);
 }
-// slice a (0-based: bits 49 - 7a .. 55 - 7a of F) as a float bit pattern
+// slice a (0-based: bits 56 - 7a .. 62 - 7a of F) as a float bit pattern
 __device__ __forceinline__ uint32_t slice_bits(uint64_t F, int a, uint32_t ms, float undo) {
     const uint32_t hi = (uint32_t)(F >> 32), lo = (uint32_t)F;
     uint32_t s;
     switch (a) {
-        case 0: s = hi >> 17; break;
-        case 1: s = hi >> 10; break;
-        case 2: s = hi >> 3; break;
-        case 3: s = __funnelshift_r(lo, hi, 28); break;
-        case 4: s = lo >> 21; break;
-        case 5: s = lo >> 14; break;
-        case 6: s = lo >> 7; break;
+        case 0: s = hi >> 24; break;
+        case 1: s = hi >> 17; break;
+        case 2: s = hi >> 10; break;
+        case 3: s = hi >> 3; break;
+        case 4: s = __funnelshift_r(lo, hi, 28); break;
+        case 5: s = lo >> 21; break;
+        case 6: s = lo >> 14; break;
+        case 7: s = lo >> 7; break;
         default: s = lo; break;
     }
     return slice_f32_bits(s, ms, undo);
@@ -162,15 +191,16 @@ __device__ __forceinline__ uint32_t pack_bf16(uint32_t f0, uint32_t f1) {
 // ---- the update -------------------------------------------------------------------------
 // One persistent CTA per SM, warp-specialised:
 //   warps 0-7  (slicers): per 128-row tile, load the tile's X values (each thread half a row,
-//              P/2 values), take the row binade, and cut the values into the eight slices,
+//              P/2 values), take the row binade, and cut the values into the nine slices,
 //              one K-step (16 columns) at a time, into a ring of kStages shared stages;
 //   warp 8     (MMA): per K-step one thread issues one MMA per X slice a, against the C
-//              slices 1 .. 9 - a stacked along N (N = (9 - a) Q), starting at the columns of
-//              group a + 1, so every pair (a, b) accumulates into group a + b; one of two
-//              tensor-memory accumulator sets; each stage is committed back to the slicers
-//              and each finished tile to the epilogue;
+//              slices 1 .. 10 - a stacked along N (N = (10 - a) Q, in pieces of <= 256),
+//              starting at the columns of group a + 1, so every pair (a, b) accumulates into
+//              group a + b; one of kSets tensor-memory accumulator sets (two when 2 x 9 Q
+//              columns fit in 512); each stage is committed back to the slicers and each
+//              finished tile to the epilogue;
 //   warps 9-12 (epilogue): lane quarter w % 4 reads its 32 rows of the finished set,
-//              combines the eight groups, applies scale and subtraction and writes OUT;
+//              combines the nine groups, applies scale and subtraction and writes OUT;
 //   warp 13    (prefetch): while the slicers start tile k it asks L2 for the X and Y rows
 //              of tile k + 2 (bulk prefetches), so the slicers' and the epilogue's loads
 //              find their rows in L2 and HBM streams without gaps.
@@ -193,14 +223,15 @@ struct UpdShape {
     static constexpr int kSliceStage = kTile * kKS * 2;            // one slice of one stage
     static constexpr int kStageBytes = kSlices * kSliceStage;      // 32 KB
     static constexpr int kSliceB = Q * P * 2;                      // one slice of C
-    // the eight C slices are stacked along N (B row (b - 1) Q + q), so one MMA of N =
-    // (9 - a) Q per X slice a deposits every pair (a, b) into group a + b
+    // the nine C slices are stacked along N (B row (b - 1) Q + q), so one MMA of N =
+    // (10 - a) Q per X slice a deposits every pair (a, b) into group a + b
     static constexpr int kOffB = kStages * kStageBytes;
     static constexpr int kSmem = kOffB + kSlices * kSliceB + 1024;  // + alignment slack
     static constexpr int kLboA = (kTile / 8) * 128;                // next 8 columns of A
     static constexpr int kLboB = (kSlices * Q / 8) * 128;          // next 8 columns of B
     static constexpr uint32_t kAcc = (uint32_t)(kGroups * Q);      // columns of one set
-    static constexpr uint32_t kCols = 2 * kAcc;                    // two sets
+    static constexpr int kSets = 2 * kAcc <= 512 ? 2 : 1;          // accumulator sets
+    static constexpr uint32_t kCols = 512;                         // allocated columns
     static constexpr int kKSteps = P / kKS;
 };
 
@@ -281,7 +312,7 @@ k_oz_update(MB<const double> X, const double* __restrict__ C, MB<const double> Y
     extern __shared__ __align__(1024) unsigned char oz_raw[];
     unsigned char* sm = oz_raw + ((1024 - (bulk::smem_addr(oz_raw) & 1023)) & 1023);
     __shared__ __align__(8) uint64_t full[kStages], empty[kStages];
-    __shared__ __align__(8) uint64_t acc_full[2], acc_empty[2], erow_full[2], fin;
+    __shared__ __align__(8) uint64_t acc_full[2], acc_empty[2], erow_full[2], erow_empty[2], fin;
     __shared__ uint32_t tslot;
     __shared__ int erow[2][kTile];
     __shared__ int fcol[Q];
@@ -300,6 +331,7 @@ k_oz_update(MB<const double> X, const double* __restrict__ C, MB<const double> Y
             bulk::mbar_init(&acc_full[b], 1);
             bulk::mbar_init(&acc_empty[b], 4);
             bulk::mbar_init(&erow_full[b], kSlicerWarps);
+            bulk::mbar_init(&erow_empty[b], 4);
         }
         bulk::mbar_init(&fin, 1);
         abort_flag = 0;
@@ -316,7 +348,7 @@ k_oz_update(MB<const double> X, const double* __restrict__ C, MB<const double> Y
     for (int e = tid; e < P * Q; e += blockDim.x) {
         const int k = e / Q, q = e - k * Q;
         const double c = C[(int64_t)k * Q + q];
-        const uint64_t F = fixed56(c, fcol[q]);
+        const uint64_t F = fixed63(c, fcol[q]);
         const bool neg = (__double_as_longlong(c) >> 63) != 0;
         const uint32_t ms = sign_magic(neg);
         const float undo = sign_undo(neg);
@@ -342,8 +374,8 @@ k_oz_update(MB<const double> X, const double* __restrict__ C, MB<const double> Y
         int stage = 0;
         int lt = 0;
         for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++lt) {
-            const int buf = lt & 1;
-            if (lt >= 2 && !wait_or_abort(&acc_empty[buf], ((lt >> 1) - 1) & 1, &abort_flag))
+            const int buf = lt & 1;   // row-binade buffer (two tiles in flight)
+            if (lt >= 2 && !wait_or_abort(&erow_empty[buf], ((lt >> 1) - 1) & 1, &abort_flag))
                 break;
             if (tid == 0) started = lt + 1;
             const int64_t i = tile * kTile + r;
@@ -382,7 +414,7 @@ k_oz_update(MB<const double> X, const double* __restrict__ C, MB<const double> Y
 #pragma unroll
                 for (int u = 0; u < 8; ++u) {
                     const double x = xv[j * 8 + u];
-                    F[u] = fixed56(x, e);
+                    F[u] = fixed63(x, e);
                     const bool neg = (__double_as_longlong(x) >> 63) != 0;
                     ms[u] = sign_magic(neg);
                     undo[u] = sign_undo(neg);
@@ -415,12 +447,11 @@ k_oz_update(MB<const double> X, const double* __restrict__ C, MB<const double> Y
             int stage = 0;
             int lt = 0;
             for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++lt) {
-                const int buf = lt & 1;
-                if (lt >= 2 &&
-                    !wait_or_abort(&acc_empty[buf], ((lt >> 1) - 1) & 1, &abort_flag))
+                const int set = lt % S::kSets, use = lt / S::kSets;
+                if (use >= 1 && !wait_or_abort(&acc_empty[set], (use - 1) & 1, &abort_flag))
                     break;
                 tc_fence_after();
-                const uint32_t dacc = tbase + (uint32_t)buf * S::kAcc;
+                const uint32_t dacc = tbase + (uint32_t)set * S::kAcc;
                 bool ok = true;
                 for (int j = 0; j < S::kKSteps; ++j) {
                     const int slot = stage % kStages, use = stage / kStages;
@@ -429,22 +460,27 @@ k_oz_update(MB<const double> X, const double* __restrict__ C, MB<const double> Y
                         break;
                     }
                     tc_fence_after();
-                    const uint64_t bd = smem_desc(sB + j * 2 * S::kLboB, S::kLboB, 128);
 #pragma unroll
                     for (int a = 1; a <= kSlices; ++a) {
-                        // X slice a times C slices 1 .. 9 - a: pair (a, b) lands in the
-                        // columns of group a + b
+                        // X slice a times C slices 1 .. 10 - a (B rows 0 .. (10 - a) Q): pair
+                        // (a, b) lands in the columns of group a + b; N in pieces of <= 256
                         const uint64_t ad = smem_desc(
                             sA + slot * S::kStageBytes + (a - 1) * S::kSliceStage, S::kLboA, 128);
-                        mma_bf16(dacc + (uint32_t)((a - 1) * Q), ad, bd,
-                                 idesc_bf16_f32(kTile, (kGroups + 1 - a) * Q),
-                                 (j > 0 || a > 1) ? 1u : 0u);
+                        const int na = (kGroups + 1 - a) * Q;
+#pragma unroll
+                        for (int n0 = 0; n0 < na; n0 += kMaxN) {
+                            const int nn = (na - n0) < kMaxN ? (na - n0) : kMaxN;
+                            const uint64_t bd = smem_desc(
+                                sB + j * 2 * S::kLboB + (n0 / 8) * 128, S::kLboB, 128);
+                            mma_bf16(dacc + (uint32_t)((a - 1) * Q + n0), ad, bd,
+                                     idesc_bf16_f32(kTile, nn), (j > 0 || a > 1) ? 1u : 0u);
+                        }
                     }
                     mma_commit(&empty[slot]);
                     ++stage;
                 }
                 if (!ok) break;
-                mma_commit(&acc_full[buf]);
+                mma_commit(&acc_full[set]);
             }
             // every MMA issued has completed before the tensor memory is released
             mma_commit(&fin);
@@ -467,13 +503,15 @@ k_oz_update(MB<const double> X, const double* __restrict__ C, MB<const double> Y
         const int m = qd * 32 + lane;
         int lt = 0;
         for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++lt) {
-            const int buf = lt & 1, use = lt >> 1;
-            if (!wait_or_abort(&acc_full[buf], use & 1, &abort_flag)) break;
-            if (!wait_or_abort(&erow_full[buf], use & 1, &abort_flag)) break;
+            const int buf = lt & 1, set = lt % S::kSets;
+            if (!wait_or_abort(&acc_full[set], (lt / S::kSets) & 1, &abort_flag)) break;
+            if (!wait_or_abort(&erow_full[buf], (lt >> 1) & 1, &abort_flag)) break;
             tc_fence_after();
             const int64_t ri = tile * kTile + m;
             const int er = erow[buf][m];
-            const uint32_t taddr = tbase + ((uint32_t)(qd * 32) << 16) + (uint32_t)buf * S::kAcc;
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&erow_empty[buf]);
+            const uint32_t taddr = tbase + ((uint32_t)(qd * 32) << 16) + (uint32_t)set * S::kAcc;
 #pragma unroll 1
             for (int col0 = 0; col0 < Q; col0 += 8) {
                 float g[kGroups][8];
@@ -499,20 +537,12 @@ k_oz_update(MB<const double> X, const double* __restrict__ C, MB<const double> Y
                     double ov[8];
 #pragma unroll
                     for (int u = 0; u < 8; ++u) {
-                        long long hi = 0, lo = 0;
+                        float gu[kGroups];
 #pragma unroll
-                        for (int gi = 0; gi < 4; ++gi)
-                            hi = hi * 128 + (long long)__float2int_rn(g[gi][u]);
-#pragma unroll
-                        for (int gi = 4; gi < 8; ++gi)
-                            lo = lo * 128 + (long long)__float2int_rn(g[gi][u]);
-                        const long long v7 = hi * (1ll << 21) + (lo >> 7);
-                        const int ex = er + fcol[col0 + u] - 1077;
-                        const double scale =
-                            ex < 1 ? 0.0
-                                   : (ex > 2046 ? __longlong_as_double(0x7FF0000000000000ll)
-                                                : __longlong_as_double((long long)ex << 52));
-                        ov[u] = fma((double)(beta_on ? -v7 : v7), scale, yv[u]);
+                        for (int gi = 0; gi < kGroups; ++gi) gu[gi] = g[gi][u];
+                        const long long v = combine_groups(gu);
+                        const double scale = pow2_biased(er + fcol[col0 + u] - 1077);
+                        ov[u] = fma((double)(beta_on ? -v : v), scale, yv[u]);
                     }
                     double2* orow = reinterpret_cast<double2*>(OUT.blk(0) + ri * OUT.w + col0);
 #pragma unroll
@@ -521,7 +551,7 @@ k_oz_update(MB<const double> X, const double* __restrict__ C, MB<const double> Y
             }
             tc_fence_before();
             __syncwarp();
-            if (lane == 0) mbar_arrive(&acc_empty[buf]);
+            if (lane == 0) mbar_arrive(&acc_empty[set]);
         }
     }
     __syncthreads();
@@ -536,8 +566,8 @@ k_oz_update(MB<const double> X, const double* __restrict__ C, MB<const double> Y
 // C = X^T Y over the n rows (CGS coefficients Q^T (A W), the A-CholQR Gram W^T (A W)):
 // X n x P (P <= 64, padded to the MMA's M = 64), Y n x Q (Q = 16 or 32).  The contraction
 // runs over rows, in tiles of 64 rows: every column of X and of Y is scaled by its binade
-// over the tile (e_p, f_q), so a tile's eight groups are exact in fp32 (<= 8 pairs x 64
-// rows x 127^2 < 2^23), and the epilogue adds the tile's V 2^{e_p + f_q - 2100} into a
+// over the tile (e_p, f_q), so a tile's nine groups are exact in fp32 (<= 9 pairs x 64
+// rows x 127^2 < 2^24), and the epilogue adds the tile's (V >> 14) 2^{e_p + f_q - 2100} into a
 // float64 accumulator per output held in registers across the CTA's tiles.  Each CTA writes
 // its P x Q partial sum; k_gram_reduce adds the partials in CTA order.
 //   warp 7     (producer): one thread copies the tile's rows of every X block and of Y
@@ -548,7 +578,7 @@ k_oz_update(MB<const double> X, const double* __restrict__ C, MB<const double> Y
 //              tile from the raw buffer (a shared max over the two row parities), pass 2
 //              cuts 8 rows x 1 column per thread and K-step into the stage ring;
 //   warp 6     (MMA): per K-step one MMA per X slice a (M = 64, K = 16) against the Y
-//              slices 1 .. 9 - a stacked along N, into the columns of groups a + 1 .. 9;
+//              slices 1 .. 10 - a stacked along N, into the columns of groups a + 1 .. 10;
 //   warps 8-11 (epilogue): M = 64 keeps rows 16 q' .. 16 q' + 15 of D in lanes 0-15 of lane
 //              quarter q', so lanes 0-15 of warp 8 + q' own the outputs p = 16 q' + lane.
 constexpr int kGramThreads = 12 * 32;
@@ -574,7 +604,8 @@ struct GramShape {
     static constexpr int kLboA = (kM / 8) * 128;
     static constexpr int kLboB = (kSlices * Q / 8) * 128;          // Y slices stacked in N
     static constexpr uint32_t kAcc = (uint32_t)(kGroups * Q);
-    static constexpr uint32_t kCols = 2 * kAcc;
+    static constexpr int kSets = 2 * kAcc <= 512 ? 2 : 1;          // accumulator sets
+    static constexpr uint32_t kCols = 512;
     static constexpr int kT = P + Q;                               // columns sliced per row
     static constexpr int kNB = (kT + 31) / 32;                     // column blocks
     static constexpr int kSlicers = 2 * kNB;                       // slicer warps (<= 6)
@@ -590,7 +621,7 @@ k_oz_gram(MB<const double> X, MB<const double> Y, int64_t n, double* __restrict_
     extern __shared__ __align__(1024) unsigned char oz_raw[];
     unsigned char* sm = oz_raw + ((1024 - (bulk::smem_addr(oz_raw) & 1023)) & 1023);
     __shared__ __align__(8) uint64_t full[kGramStages], empty[kGramStages];
-    __shared__ __align__(8) uint64_t acc_full[2], acc_empty[2], cexp_full[2], fin;
+    __shared__ __align__(8) uint64_t acc_full[2], acc_empty[2], cexp_full[2], cexp_empty[2], fin;
     __shared__ __align__(8) uint64_t raw_full[2], raw_empty[2];
     __shared__ uint32_t tslot;
     __shared__ int cexp[2][S::kT];          // tile binades: X columns, then Y columns
@@ -613,6 +644,7 @@ k_oz_gram(MB<const double> X, MB<const double> Y, int64_t n, double* __restrict_
             bulk::mbar_init(&acc_full[b], 1);
             bulk::mbar_init(&acc_empty[b], 4);
             bulk::mbar_init(&cexp_full[b], S::kSlicers);
+            bulk::mbar_init(&cexp_empty[b], 4);
             bulk::mbar_init(&raw_full[b], 1);
             bulk::mbar_init(&raw_empty[b], S::kSlicers);
         }
@@ -646,9 +678,9 @@ k_oz_gram(MB<const double> X, MB<const double> Y, int64_t n, double* __restrict_
         int lt = 0;
         bool failed = false;   // the slicer warps leave together (they share named barriers)
         for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++lt) {
-            const int buf = lt & 1;
+            const int buf = lt & 1;   // binade / raw buffer (two tiles in flight)
             if (lt >= 2 && !failed &&
-                !wait_or_abort(&acc_empty[buf], ((lt >> 1) - 1) & 1, &abort_flag))
+                !wait_or_abort(&cexp_empty[buf], ((lt >> 1) - 1) & 1, &abort_flag))
                 failed = true;
             if (!failed && !wait_or_abort(&raw_full[buf], (lt >> 1) & 1, &abort_flag))
                 failed = true;
@@ -689,7 +721,7 @@ k_oz_gram(MB<const double> X, MB<const double> Y, int64_t n, double* __restrict_
 #pragma unroll
                     for (int u = 0; u < 8; ++u) {
                         const double x = (rb + u < rows) ? raw[(rb + u) * w] : 0.0;
-                        F[u] = fixed56(x, e);
+                        F[u] = fixed63(x, e);
                         const bool neg = (__double_as_longlong(x) >> 63) != 0;
                         ms[u] = sign_magic(neg);
                         undo[u] = sign_undo(neg);
@@ -748,12 +780,11 @@ k_oz_gram(MB<const double> X, MB<const double> Y, int64_t n, double* __restrict_
             int stage = 0;
             int lt = 0;
             for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++lt) {
-                const int buf = lt & 1;
-                if (lt >= 2 &&
-                    !wait_or_abort(&acc_empty[buf], ((lt >> 1) - 1) & 1, &abort_flag))
+                const int set = lt % S::kSets, use = lt / S::kSets;
+                if (use >= 1 && !wait_or_abort(&acc_empty[set], (use - 1) & 1, &abort_flag))
                     break;
                 tc_fence_after();
-                const uint32_t dacc = tbase + (uint32_t)buf * S::kAcc;
+                const uint32_t dacc = tbase + (uint32_t)set * S::kAcc;
                 bool ok = true;
                 for (int ks = 0; ks < S::kKSteps; ++ks) {
                     const int slot = stage % kGramStages, use = stage / kGramStages;
@@ -763,19 +794,24 @@ k_oz_gram(MB<const double> X, MB<const double> Y, int64_t n, double* __restrict_
                     }
                     tc_fence_after();
                     const uint32_t st = sbase + slot * S::kStageBytes;
-                    const uint64_t bd = smem_desc(st + S::kOffB, S::kLboB, 128);
 #pragma unroll
                     for (int a = 1; a <= kSlices; ++a) {
                         const uint64_t ad = smem_desc(st + (a - 1) * S::kSliceA, S::kLboA, 128);
-                        mma_bf16(dacc + (uint32_t)((a - 1) * Q), ad, bd,
-                                 idesc_bf16_f32(S::kM, (kGroups + 1 - a) * Q),
-                                 (ks > 0 || a > 1) ? 1u : 0u);
+                        const int na = (kGroups + 1 - a) * Q;
+#pragma unroll
+                        for (int n0 = 0; n0 < na; n0 += kMaxN) {
+                            const int nn = (na - n0) < kMaxN ? (na - n0) : kMaxN;
+                            const uint64_t bd =
+                                smem_desc(st + S::kOffB + (n0 / 8) * 128, S::kLboB, 128);
+                            mma_bf16(dacc + (uint32_t)((a - 1) * Q + n0), ad, bd,
+                                     idesc_bf16_f32(S::kM, nn), (ks > 0 || a > 1) ? 1u : 0u);
+                        }
                     }
                     mma_commit(&empty[slot]);
                     ++stage;
                 }
                 if (!ok) break;
-                mma_commit(&acc_full[buf]);
+                mma_commit(&acc_full[set]);
             }
             mma_commit(&fin);
             bulk::mbar_wait(&fin, 0);
@@ -791,40 +827,37 @@ k_oz_gram(MB<const double> X, MB<const double> Y, int64_t n, double* __restrict_
         for (int q = 0; q < Q; ++q) acc[q] = 0.0;
         int lt = 0;
         for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++lt) {
-            const int buf = lt & 1, use = lt >> 1;
-            if (!wait_or_abort(&acc_full[buf], use & 1, &abort_flag)) break;
-            if (!wait_or_abort(&cexp_full[buf], use & 1, &abort_flag)) break;
+            const int buf = lt & 1, set = lt % S::kSets;
+            if (!wait_or_abort(&acc_full[set], (lt / S::kSets) & 1, &abort_flag)) break;
+            if (!wait_or_abort(&cexp_full[buf], (lt >> 1) & 1, &abort_flag)) break;
             tc_fence_after();
             const int ep = own ? cexp[buf][p] : 0;
-            const uint32_t taddr = tbase + ((uint32_t)(qd * 32) << 16) + (uint32_t)buf * S::kAcc;
+            int fq[Q];
 #pragma unroll
-            for (int col0 = 0; col0 < Q; col0 += 8) {
-                float g[kGroups][8];
+            for (int q = 0; q < Q; ++q) fq[q] = cexp[buf][P + q];
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&cexp_empty[buf]);
+            const uint32_t taddr = tbase + ((uint32_t)(qd * 32) << 16) + (uint32_t)set * S::kAcc;
+#pragma unroll
+            for (int col0 = 0; col0 < Q; col0 += 4) {
+                float g[kGroups][4];
 #pragma unroll
                 for (int gi = 0; gi < kGroups; ++gi)
-                    tmem_ld8(taddr + (uint32_t)(gi * Q + col0), g[gi]);
+                    tmem_ld4(taddr + (uint32_t)(gi * Q + col0), g[gi]);
                 tmem_wait_ld();
 #pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    long long hi = 0, lo = 0;
+                for (int u = 0; u < 4; ++u) {
+                    float gu[kGroups];
 #pragma unroll
-                    for (int gi = 0; gi < 4; ++gi)
-                        hi = hi * 128 + (long long)__float2int_rn(g[gi][u]);
-#pragma unroll
-                    for (int gi = 4; gi < 8; ++gi)
-                        lo = lo * 128 + (long long)__float2int_rn(g[gi][u]);
-                    const long long v7 = hi * (1ll << 21) + (lo >> 7);
-                    const int ex = ep + cexp[buf][P + col0 + u] - 1077;
-                    const double scale =
-                        ex < 1 ? 0.0
-                               : (ex > 2046 ? __longlong_as_double(0x7FF0000000000000ll)
-                                            : __longlong_as_double((long long)ex << 52));
-                    acc[col0 + u] = fma((double)v7, scale, acc[col0 + u]);
+                    for (int gi = 0; gi < kGroups; ++gi) gu[gi] = g[gi][u];
+                    const long long v = combine_groups(gu);
+                    acc[col0 + u] =
+                        fma((double)v, pow2_biased(ep + fq[col0 + u] - 1077), acc[col0 + u]);
                 }
             }
             tc_fence_before();
             __syncwarp();
-            if (lane == 0) mbar_arrive(&acc_empty[buf]);
+            if (lane == 0) mbar_arrive(&acc_empty[set]);
         }
         if (own) {
             double* out = partials + (int64_t)blockIdx.x * 4096 + p * Q;

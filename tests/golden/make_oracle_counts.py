@@ -8,6 +8,7 @@ Usage: python tests/golden/make_oracle_counts.py [workload ...]   (ani3d, sky3d,
        python tests/golden/make_oracle_counts.py --s S workload       (one s of a workload)
        python tests/golden/make_oracle_counts.py --perturbed SEED workload
        python tests/golden/make_oracle_counts.py diff2d
+       python tests/golden/make_oracle_counts.py --perturbed SEED diff2d   (target solve)
 
 The diff2d form records the differentiable workload (2D diffusion 512^2, kappa = exp of a
 Gaussian random field, t = 16, s = 3): the solve for the target x* (field seed 5, b = 1),
@@ -53,7 +54,25 @@ def store(key, value):
         json.dump(data, open(OUT, "w"), indent=1, sort_keys=True)
 
 
+def diff2d_target_perturbed(seed):
+    """The differentiable workload's target solve (field seed 5, b = 1) with b multiplied
+    entrywise by (1 + 1e-15 xi): its iteration count under rounding-level changes."""
+    N, t, s = DIFF2D_N, DIFF2D_T, DIFF2D_S
+    lk_star = wl.kappa_gaussian_field2d(N, seed=5, corr=16.0)
+    A = wl.stencil_matrix((N, N), kappa=np.exp(lk_star))
+    part = wl.partition_boxes((N, N), t)
+    rng = np.random.default_rng(seed)
+    b = 1.0 + 1e-15 * rng.standard_normal(N * N)
+    t0 = time.time()
+    res = o.solve(A, b, part, t, s, tol=1e-8, maxit=20000, variant="sre")
+    key = f"diff2d/N{N}/t{t}/s{s}/sre/sstep/fp64/target/perturbed/{seed}"
+    store(key, dict(iters=res.iters, status=res.status, seconds=round(time.time() - t0, 2)))
+    print(key, res.iters, flush=True)
+
+
 def perturbed(seed, name):
+    if name == "diff2d":
+        return diff2d_target_perturbed(seed)
     cfg = RUNS[name]
     p = cfg["make"]()
     rng = np.random.default_rng(seed)

@@ -92,3 +92,58 @@ def test_grad_logkappa_matches_finite_differences():
         fd = (loss_dense(lk0.ravel() + e) - loss_dense(lk0.ravel() - e)) / (2 * h)
         assert abs(g[p] - fd) <= 1e-6 * np.abs(g).max() + 1e-8 * abs(fd), (p, g[p], fd)
     S.close()
+
+
+@pytest.mark.slow
+def test_differentiable_workload_full_size_against_oracle_record():
+    """The differentiable configuration at its full size (512^2, kappa = exp of a Gaussian
+    random field with correlation length 16, t = 16, s = 3, tol 1e-8): the solve for the
+    target x* (field seed 5, b = 1), the forward solve x (field seed 4, b = 1), the adjoint
+    solve A lambda = x - x* and dL/dlog kappa, each against the oracle's whole-solve record
+    (tests/golden/oracle_counts.json, written by the oracle only): iteration counts within
+    one, the first 21 residual norms to 1e-6, the true relative residual, and x, lambda
+    and the gradient at 256 sampled rows (float64 tolerances relative to the max-norm of
+    the oracle's vector: 1e-8 for x*, x and lambda, 1e-7 for the gradient, a product of
+    two solutions)."""
+    import json
+    gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden",
+                                       "oracle_counts.json")))
+    key = "diff2d/N512/t16/s3/sre/sstep/fp64"
+    N, t, s = 512, 16, 3
+    lk = wl.kappa_gaussian_field2d(N, seed=4, corr=16.0)
+    lk_star = wl.kappa_gaussian_field2d(N, seed=5, corr=16.0)
+    A = wl.stencil_matrix((N, N), kappa=np.exp(lk))
+    A_star = wl.stencil_matrix((N, N), kappa=np.exp(lk_star))
+    part = wl.partition_boxes((N, N), t)
+    S = ekcg.Solver(A, t, part, max_s=s)
+    val = torch.empty(A.nnz, dtype=torch.float64, device="cuda")
+    one = torch.ones(N * N, dtype=torch.float64, device="cuda")
+
+    def solve(log_k, rhs, rec, Amat, rhs_np):
+        ekcg.ekcg_diffusion2d_values(S.ctx, N, N, 1.0, 1.0,
+                                     torch.as_tensor(log_k.ravel(), device="cuda"), val)
+        ekcg.ekcg_update_values(S.ctx, val)
+        x, it, hist, st = S.solve(rhs, s=s, tol=1e-8, maxit=5000)
+        assert st == 0 and abs(it - rec["iters"]) <= 1, (it, rec["iters"])
+        np.testing.assert_allclose(hist[:21], rec["hist"][:21], rtol=1e-6)
+        xh = x.cpu().numpy()
+        assert (np.linalg.norm(rhs_np - Amat.to_scipy() @ xh) <= 1.01e-8 *
+                np.linalg.norm(rhs_np))
+        ref = np.array(rec["x"]["values"])
+        rows = np.array(gold[key + "/grad_logkappa"]["rows"])
+        assert np.max(np.abs(xh[rows] - ref)) <= 1e-8 * rec["x"]["norminf"]
+        return x, xh
+
+    xs, xsh = solve(lk_star, one, gold[key + "/target"], A_star, np.ones(N * N))
+    x, xh = solve(lk, one, gold[key + "/forward"], A, np.ones(N * N))
+    g = x - xs
+    lam, lamh = solve(lk, g.contiguous(), gold[key + "/adjoint"], A, g.cpu().numpy())
+    glk = torch.empty(N * N, dtype=torch.float64, device="cuda")
+    ekcg.ekcg_diffusion2d_grad_logkappa(S.ctx, N, N, 1.0, 1.0,
+                                        torch.as_tensor(lk.ravel(), device="cuda"), lam, x, glk)
+    rec = gold[key + "/grad_logkappa"]
+    rows = np.array(rec["rows"])
+    got = glk.cpu().numpy()[rows]
+    assert np.max(np.abs(got - np.array(rec["values"]))) <= 1e-7 * rec["norminf"]
+    np.testing.assert_allclose(0.5 * float((g * g).sum()), rec["loss"], rtol=1e-7)
+    S.close()

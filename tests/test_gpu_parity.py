@@ -426,6 +426,27 @@ def test_ani3d_full_size_sampled():
 
 
 @pytest.mark.slow
+@pytest.mark.parametrize("s", [1, 4, 8])
+def test_ani3d_full_size_other_s_against_oracle_records(s):
+    """Ani3D-like 128^3, t = 32, s = 1, 4, 8 (the configuration's other s values): the
+    iteration count within one of the oracle's whole-solve record (tests/golden/
+    oracle_counts.json, written by the oracle only), the first 21 residual norms to 1e-6
+    and the true relative residual."""
+    import json
+    gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden",
+                                       "oracle_counts.json")))
+    g = gold[f"ani3d/t32/s{s}/sre/sstep/fp64"]
+    p = wl.ani3d(128, 32, seed=1)
+    S = ekcg.Solver(p.A, 32, p.part, max_s=s)
+    x, it, hist, st = S.solve(dev(p.b), s=s, tol=1e-8, maxit=5000)
+    assert st == 0
+    assert abs(it - g["iters"]) <= 1, (it, g["iters"])
+    np.testing.assert_allclose(hist[:21], g["hist"][:21], rtol=1e-6)
+    assert relres(p.A, p.b, x.cpu().numpy()) <= 1e-8 * 1.01
+    S.close()
+
+
+@pytest.mark.slow
 def test_sky3d_full_size_against_oracle_record():
     """Sky3D-like 96^3 (coefficient 1 / 1e3 on 8^3 blocks), t = 16, s = 4, float64: the
     iteration count within one of the oracle's whole-solve record
@@ -444,6 +465,30 @@ def test_sky3d_full_size_against_oracle_record():
     np.testing.assert_allclose(hist[:21], g["hist"][:21], rtol=1e-6)
     assert relres(p.A, p.b, x.cpu().numpy()) <= 1e-8 * 1.01
     S.close()
+
+
+@pytest.mark.slow
+def test_sky3d_full_size_perturbed_counts_within_oracle_spread():
+    """The Sky3D-like count is sensitive to rounding: with b multiplied entrywise by
+    (1 + 1e-15 xi) the oracle itself takes 452 - 457 iterations (tests/golden/
+    oracle_counts.json, "perturbed" records, written by the oracle only).  With the same
+    perturbations, every GPU count must lie within that spread widened by one."""
+    import json
+    gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden",
+                                       "oracle_counts.json")))
+    key = "sky3d/t16/s4/sre/sstep/fp64"
+    seeds = sorted(int(k.rsplit("/", 1)[1]) for k in gold if k.startswith(key + "/perturbed/"))
+    counts = [gold[key]["iters"]] + [gold[f"{key}/perturbed/{sd}"]["iters"] for sd in seeds]
+    p = wl.sky3d(96, 16, seed=2)
+    S = ekcg.Solver(p.A, 16, p.part, max_s=4)
+    got = []
+    for sd in seeds:
+        b = p.b * (1.0 + 1e-15 * np.random.default_rng(sd).standard_normal(p.A.n))
+        x, it, hist, st = S.solve(dev(b), s=4, tol=1e-8, maxit=5000)
+        assert st == 0
+        got.append(it)
+    S.close()
+    assert all(min(counts) - 1 <= it <= max(counts) + 1 for it in got), (got, counts)
 
 
 def test_bounded_wait_reports_timeout_and_device_stays_usable():
