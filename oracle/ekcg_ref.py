@@ -36,7 +36,12 @@ Readings where the paper is silent or refers to the author's thesis:
   * Stopping rule: while rho > tol*rho0 and iterations < maxit, rho = ||r_k||_2 of the
     recursively updated residual, checked once per s-step iteration.
   * Breakdown: a Cholesky pivot d_i <= breakdown_tol * |G_ii| (or a non-finite one) stops
-    the solve with status BREAKDOWN and the current iterate.
+    the solve with status BREAKDOWN and the current iterate.  With deflate=True (A-CholQR
+    only) such a column is instead deflated, as enlarged CG deflates dependent directions
+    (Section 2, the reference to ECG): it is dropped from the block (set to zero in W and
+    A W, no Schur update from it), the other columns are A-orthonormalised among
+    themselves, and the solve continues with fewer directions; a non-finite pivot, or a
+    block whose columns are all deflated, is still a breakdown.
   * CA SRE-CG window: the last (s+1)t basis vectors; CA SRE-CG2 / (CA) MSDO-CG: all.
   * Inside a CA block V the columns are power-major: column p*t + i belongs to A^p W_i.
 """
@@ -101,30 +106,50 @@ def split_T(r: np.ndarray, part: np.ndarray, t: int) -> np.ndarray:
 # A-orthonormalisation (Section 3.1 and Section 4: CGS2 + A-CholQR or Pre-CholQR)
 # ----------------------------------------------------------------------------------------
 
-def cholesky_upper(G: np.ndarray, breakdown_tol: float) -> np.ndarray:
+def cholesky_upper(G: np.ndarray, breakdown_tol: float, deflate: bool = False):
     """Upper Cholesky factor R (G = R^T R) from the upper triangle of G, right-looking.
-    Breakdown rule: pivot d_i <= breakdown_tol*|G_ii| or non-finite."""
+    Breakdown rule: pivot d_i <= breakdown_tol*|G_ii| or non-finite.  With deflate=True a
+    finite pivot that fails the rule drops column i instead: row i of R becomes e_i^T (no
+    Schur update from it) and i is listed in the returned `dropped`; then (R, dropped) is
+    returned, and a block with every column dropped is a breakdown."""
     m = G.shape[0]
     S = np.triu(np.array(G, dtype=np.float64))
     R = np.zeros((m, m))
+    dropped = []
     for i in range(m):
         d = S[i, i]
         if not np.isfinite(d) or d <= breakdown_tol * abs(G[i, i]):
-            raise Breakdown(f"pivot {i}: {d!r} vs G_ii {G[i, i]!r}")
+            if not deflate or not np.isfinite(d):
+                raise Breakdown(f"pivot {i}: {d!r} vs G_ii {G[i, i]!r}")
+            R[i, i] = 1.0
+            dropped.append(i)
+            continue
         R[i, i] = math.sqrt(d)
         R[i, i + 1:] = S[i, i + 1:] / R[i, i]
         S[i + 1:, i + 1:] -= np.triu(np.outer(R[i, i + 1:], R[i, i + 1:]))
-    return R
+    if not deflate:
+        return R
+    if len(dropped) == m:
+        raise Breakdown("every column of the block deflated")
+    return R, dropped
 
 
-def right_solve_upper(W: np.ndarray, R: np.ndarray) -> np.ndarray:
-    """W R^{-1} for upper-triangular R (solves X R = W)."""
-    return sla.solve_triangular(R, W.T, trans="T", lower=False).T
+def right_solve_upper(W: np.ndarray, R: np.ndarray, dropped=()) -> np.ndarray:
+    """W R^{-1} for upper-triangular R (solves X R = W); the columns in `dropped`
+    (deflated by cholesky_upper) are set to zero."""
+    X = sla.solve_triangular(R, W.T, trans="T", lower=False).T
+    if len(dropped):
+        X[:, list(dropped)] = 0.0
+    return X
 
 
-def a_cholqr(W, AW, breakdown_tol):
-    """A-CholQR: G = W^T A W = R^T R, W <- W R^{-1} (and A W <- A W R^{-1})."""
+def a_cholqr(W, AW, breakdown_tol, deflate=False):
+    """A-CholQR: G = W^T A W = R^T R, W <- W R^{-1} (and A W <- A W R^{-1}); with
+    deflate=True the columns whose pivots fail the breakdown rule are dropped (zeroed)."""
     G = W.T @ AW
+    if deflate:
+        R, dropped = cholesky_upper(G, breakdown_tol, deflate=True)
+        return right_solve_upper(W, R, dropped), right_solve_upper(AW, R, dropped)
     R = cholesky_upper(G, breakdown_tol)
     return right_solve_upper(W, R), right_solve_upper(AW, R)
 
@@ -172,7 +197,7 @@ class _Ctx:
     bookkeeping."""
 
     def __init__(self, A, part, t, orth, breakdown_tol, explicit_AW, record, carried_cgs=False,
-                 precond=None):
+                 precond=None, deflate=False):
         self.A = A.to_scipy() if hasattr(A, "to_scipy") else sp.csr_matrix(A)
         self.part = np.asarray(part)
         self.t = t
@@ -182,6 +207,9 @@ class _Ctx:
         self.carried = carried_cgs
         self.record = record
         self.pre = precond
+        self.deflate = deflate
+        if deflate and orth != "acholqr":
+            raise ValueError("deflation is defined for A-CholQR")
         self.spmm = 0
 
     def matmul(self, W):
@@ -204,7 +232,7 @@ class _Ctx:
 
     def self_orth(self, W, AW):
         if self.orth == "acholqr":
-            W, AW = a_cholqr(W, AW, self.tol_bd)
+            W, AW = a_cholqr(W, AW, self.tol_bd, self.deflate)
         elif self.orth == "precholqr":
             W, AW = pre_cholqr(W, AW, self.tol_bd)
         else:
@@ -352,7 +380,7 @@ def cg(A, b, x0=None, tol=1e-8, maxit=10000, record=False) -> Result:
 
 def sstep_sre_cg(A, b, part, t, s, tol=1e-8, maxit=1000, x0=None, orth="acholqr",
                  full_history=False, breakdown_tol=1e-14, explicit_AW=False,
-                 record=False, carried_cgs=False, precond=None) -> Result:
+                 record=False, carried_cgs=False, precond=None, deflate=False) -> Result:
     """s-step SRE-CG (Algorithm 4); with full_history=True, s-step SRE-CG2 (Algorithm 3).
 
     Iteration k builds s blocks W_j..W_{j+s-1}, j = (k-1)s+1.  W_1 = T(r_0) is only
@@ -363,7 +391,8 @@ def sstep_sre_cg(A, b, part, t, s, tol=1e-8, maxit=1000, x0=None, orth="acholqr"
     L^{-T} T(L^{-1} r_0) and W_j = M^{-1} A W_{j-1}; the A-orthonormalisation and the
     updates are unchanged.
     """
-    ctx = _Ctx(A, part, t, orth, breakdown_tol, explicit_AW, record, carried_cgs, precond)
+    ctx = _Ctx(A, part, t, orth, breakdown_tol, explicit_AW, record, carried_cgs, precond,
+               deflate)
     x, r, rho0 = _start(A, b, x0)
     res = Result(x=x, iters=0, hist=[rho0], status=OK)
     _record(ctx, res, x, r)
@@ -417,12 +446,13 @@ def sstep_sre_cg2(*args, **kw) -> Result:
 
 def sstep_msdo_cg(A, b, part, t, s, tol=1e-8, maxit=1000, x0=None, orth="acholqr",
                   breakdown_tol=1e-14, explicit_AW=False, record=False,
-                  carried_cgs=False, precond=None) -> Result:
+                  carried_cgs=False, precond=None, deflate=False) -> Result:
     """s-step MSDO-CG (Algorithm 6).  Iteration k: W_1 = T(r_{k-1}) A-orthonormalised
     against Q (k > 1) and itself; W_{i+1} = A W_i against Q and itself, i = 1..s-1; every
     block joins V and Q.  Then alpha = V^T r_{k-1} and the x / r updates.  With a split
     preconditioner (Algorithm 10): W_1 = L^{-T} T(L^{-1} r_{k-1}), W_{i+1} = M^{-1} A W_i."""
-    ctx = _Ctx(A, part, t, orth, breakdown_tol, explicit_AW, record, carried_cgs, precond)
+    ctx = _Ctx(A, part, t, orth, breakdown_tol, explicit_AW, record, carried_cgs, precond,
+               deflate)
     x, r, rho0 = _start(A, b, x0)
     res = Result(x=x, iters=0, hist=[rho0], status=OK)
     _record(ctx, res, x, r)
@@ -469,7 +499,7 @@ def _split_blocks(V, AV, t):
 
 def ca_enlarged_cg(A, b, part, t, s, tol=1e-8, maxit=1000, x0=None, orth="acholqr",
                    variant="sre", arnoldi="alg7", breakdown_tol=1e-14, explicit_AW=False,
-                   record=False, carried_cgs=False, precond=None) -> Result:
+                   record=False, carried_cgs=False, precond=None, deflate=False) -> Result:
     """CA SRE-CG / CA SRE-CG2 / CA MSDO-CG: Algorithms 4 / 3 / 6 with the basis built by
     the CA-Arnoldi A-orthonormalisation (Algorithm 5, arnoldi='alg5') or the modified
     CA-Arnoldi (Algorithm 7, arnoldi='alg7').
@@ -487,7 +517,8 @@ def ca_enlarged_cg(A, b, part, t, s, tol=1e-8, maxit=1000, x0=None, orth="acholq
     """
     if variant not in VARIANTS or arnoldi not in ("alg5", "alg7"):
         raise ValueError((variant, arnoldi))
-    ctx = _Ctx(A, part, t, orth, breakdown_tol, explicit_AW, record, carried_cgs, precond)
+    ctx = _Ctx(A, part, t, orth, breakdown_tol, explicit_AW, record, carried_cgs, precond,
+               deflate)
     x, r, rho0 = _start(A, b, x0)
     res = Result(x=x, iters=0, hist=[rho0], status=OK)
     _record(ctx, res, x, r)
@@ -547,14 +578,14 @@ def ca_enlarged_cg(A, b, part, t, s, tol=1e-8, maxit=1000, x0=None, orth="acholq
 
 def restructured_sre_cg(A, b, part, t, s, tol=1e-8, maxit=1000, x0=None, orth="acholqr",
                         full_history=False, breakdown_tol=1e-14, record=False,
-                        carried_cgs=False) -> Result:
+                        carried_cgs=False, deflate=False) -> Result:
     """Restructured SRE-CG (Algorithm 2; Algorithm 1 with full_history=True): build the s
     blocks as in Alg. 4 / Alg. 3, then s sequential updates alpha = W_i^T r_{i-1},
     x_i = x_{i-1} + W_i alpha, r_i = r_{i-1} - A W_i alpha.  The residual norm is checked
     once every s updates; `iters` counts those outer steps (k_s of Tables 2-3).  With
     record=True, `xs` holds every inner iterate x_0, x_1, x_2, ... (for s = 1 this is
     SRE-CG / SRE-CG2 itself)."""
-    ctx = _Ctx(A, part, t, orth, breakdown_tol, False, record, carried_cgs)
+    ctx = _Ctx(A, part, t, orth, breakdown_tol, False, record, carried_cgs, None, deflate)
     x, r, rho0 = _start(A, b, x0)
     res = Result(x=x, iters=0, hist=[rho0], status=OK)
     if record:
@@ -604,25 +635,26 @@ def restructured_sre_cg(A, b, part, t, s, tol=1e-8, maxit=1000, x0=None, orth="a
 
 def solve(A, b, part, t, s, tol=1e-8, maxit=1000, x0=None, variant="sre", basis="sstep",
           orth="acholqr", breakdown_tol=1e-14, explicit_AW=False, record=False,
-          carried_cgs=False, precond=None) -> Result:
+          carried_cgs=False, precond=None, deflate=False) -> Result:
     """Select the algorithm: basis 'sstep' -> Alg. 4 (sre) / Alg. 3 (sre2) / Alg. 6 (msdo);
     basis 'ca5' / 'ca7' -> the CA form of the variant with Alg. 5 / Alg. 7.  `precond`
     (e.g. BlockJacobi) gives the split preconditioned forms of Section 5 (Algorithms 8-10).
+    deflate=True drops the columns whose A-CholQR pivots fail the breakdown rule.
     basis 'restructured' -> Alg. 2 (sre) / Alg. 1 (sre2)."""
     if basis == "restructured":
         if variant == "msdo" or precond is not None:
             raise ValueError("the restructured forms are Algorithms 1 and 2 (SRE-CG, SRE-CG2)")
         return restructured_sre_cg(A, b, part, t, s, tol, maxit, x0, orth, variant == "sre2",
-                                   breakdown_tol, record, carried_cgs)
+                                   breakdown_tol, record, carried_cgs, deflate)
     if basis == "sstep":
         if variant == "msdo":
             return sstep_msdo_cg(A, b, part, t, s, tol, maxit, x0, orth, breakdown_tol,
-                                 explicit_AW, record, carried_cgs, precond)
+                                 explicit_AW, record, carried_cgs, precond, deflate)
         return sstep_sre_cg(A, b, part, t, s, tol, maxit, x0, orth, variant == "sre2",
-                            breakdown_tol, explicit_AW, record, carried_cgs, precond)
+                            breakdown_tol, explicit_AW, record, carried_cgs, precond, deflate)
     return ca_enlarged_cg(A, b, part, t, s, tol, maxit, x0, orth, variant,
                           "alg5" if basis == "ca5" else "alg7", breakdown_tol, explicit_AW,
-                          record, carried_cgs, precond)
+                          record, carried_cgs, precond, deflate)
 
 
 # ----------------------------------------------------------------------------------------
