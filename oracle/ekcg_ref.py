@@ -232,7 +232,8 @@ class _Ctx:
 
     def self_orth(self, W, AW):
         if self.orth == "acholqr":
-            W, AW = a_cholqr(W, AW, self.tol_bd, self.deflate)
+            W, AW = (a_cholqr(W, AW, self.tol_bd, deflate=True) if self.deflate
+                     else a_cholqr(W, AW, self.tol_bd))
         elif self.orth == "precholqr":
             W, AW = pre_cholqr(W, AW, self.tol_bd)
         else:

@@ -9,6 +9,7 @@ Usage: python tests/golden/make_oracle_counts.py [workload ...]   (ani3d, sky3d,
        python tests/golden/make_oracle_counts.py --perturbed SEED workload
        python tests/golden/make_oracle_counts.py diff2d
        python tests/golden/make_oracle_counts.py --perturbed SEED diff2d   (target solve)
+       python tests/golden/make_oracle_counts.py --perturbed SEED diff2d-forward | diff2d-adjoint
 
 The diff2d form records the differentiable workload (2D diffusion 512^2, kappa = exp of a
 Gaussian random field, t = 16, s = 3): the solve for the target x* (field seed 5, b = 1),
@@ -70,9 +71,35 @@ def diff2d_target_perturbed(seed):
     print(key, res.iters, flush=True)
 
 
+def diff2d_perturbed(seed, which):
+    """The differentiable workload's forward solve (field seed 4, b = 1) or adjoint solve
+    (A lambda = x - x*, x and x* from the oracle) with the right-hand side multiplied
+    entrywise by (1 + 1e-15 xi): its iteration count under rounding-level changes."""
+    N, t, s = DIFF2D_N, DIFF2D_T, DIFF2D_S
+    lk = wl.kappa_gaussian_field2d(N, seed=4, corr=16.0)
+    A = wl.stencil_matrix((N, N), kappa=np.exp(lk))
+    part = wl.partition_boxes((N, N), t)
+    rhs = np.ones(N * N)
+    if which == "adjoint":
+        lk_star = wl.kappa_gaussian_field2d(N, seed=5, corr=16.0)
+        A_star = wl.stencil_matrix((N, N), kappa=np.exp(lk_star))
+        xs = o.solve(A_star, rhs, part, t, s, tol=1e-8, maxit=20000, variant="sre").x
+        x = o.solve(A, rhs, part, t, s, tol=1e-8, maxit=20000, variant="sre").x
+        rhs = x - xs
+    rng = np.random.default_rng(seed)
+    b = rhs * (1.0 + 1e-15 * rng.standard_normal(N * N))
+    t0 = time.time()
+    res = o.solve(A, b, part, t, s, tol=1e-8, maxit=20000, variant="sre")
+    key = f"diff2d/N{N}/t{t}/s{s}/sre/sstep/fp64/{which}/perturbed/{seed}"
+    store(key, dict(iters=res.iters, status=res.status, seconds=round(time.time() - t0, 2)))
+    print(key, res.iters, flush=True)
+
+
 def perturbed(seed, name):
     if name == "diff2d":
         return diff2d_target_perturbed(seed)
+    if name in ("diff2d-forward", "diff2d-adjoint"):
+        return diff2d_perturbed(seed, name.split("-")[1])
     cfg = RUNS[name]
     p = cfg["make"]()
     rng = np.random.default_rng(seed)
