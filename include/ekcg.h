@@ -88,11 +88,17 @@ typedef struct {
     int max_refine;       /* FP32_IR: maximum outer refinement steps                       */
     int profile;          /* 1: time every kernel class with CUDA events (ekcg_profile)   */
     int contraction;      /* EKCG_CONTRACT_FP64 / EKCG_CONTRACT_SPLIT (float64 path)      */
+    int deflate;          /* 1: rank-revealing A-CholQR.  A Cholesky pivot that fails the
+                             breakdown rule drops its column from the block (zero in W and
+                             A W, no update from it) and the solve continues with fewer
+                             directions, as enlarged CG deflates dependent search directions
+                             (Section 2); only a block whose columns all drop (or a non-finite
+                             pivot) is a breakdown.  A-CholQR only; 0 (default): stop.      */
 } ekcg_opts;
 
 /* Fill *opts with the defaults: SRE, SSTEP, ACHOLQR, FP64, max_s 8, max_blocks 0,
  * max_basis_bytes 0, breakdown_tol 1e-14, inner_tol 1e-4, max_refine 30, profile 0,
- * contraction EKCG_CONTRACT_SPLIT.                                                        */
+ * contraction EKCG_CONTRACT_SPLIT, deflate 0.                                             */
 void ekcg_default_opts(ekcg_opts* opts);
 
 /* Build a solver context for the SPD matrix A (Section 2) and its t-way partition.
@@ -190,6 +196,24 @@ int ekcg_wait_selftest(long long limit_cycles, void* stream);
  * outputs), EKCG_ENOMEM, EKCG_ECUDA.                                                      */
 int ekcg_fp64_fma_rate(void* stream, int* num_sms, double* tflops);
 
+/* Columns dropped by the rank-revealing A-CholQR (opts.deflate) in the last solve.        */
+int ekcg_deflation_stats(const ekcg_ctx* ctx, int64_t* columns);
+
+/* Device-side convergence test (the `while` line of Algorithms 3 and 4) for later solves of
+ * s-step or restructured SRE-CG in float64 (on != 0, the default) or the host-side test
+ * (on = 0).  On the device, once the basis window is full, the iterations run as a CUDA
+ * graph of conditional iterations: a one-thread kernel after each iteration compares
+ * ||r_k|| with tol ||r_0||, checks k against maxit and the breakdown / timeout status word,
+ * appends ||r_k|| to a device history and enables the next iteration; the host
+ * synchronises once per batch of up to eight iterations and copies the history at the end.
+ * The kernels, their order and their arguments are those of the host-driven loop, so
+ * results are bitwise the same.  Per-launch profiling (ekcg_set_profile) and the other
+ * variants, bases and precisions use the host loop.  Errors: EKCG_EINVAL (NULL ctx).       */
+int ekcg_set_device_loop(ekcg_ctx* ctx, int on);
+
+/* Iterations of the last solve that ran in the device loop (0: the host loop ran all).     */
+int ekcg_device_loop_stats(const ekcg_ctx* ctx, int64_t* device_iters);
+
 /* Turn the per-launch CUDA-event timing of later solves on (on != 0) or off, whatever
  * opts.profile was at setup.  Errors: EKCG_EINVAL (NULL ctx).                            */
 int ekcg_set_profile(ekcg_ctx* ctx, int on);
@@ -242,7 +266,9 @@ int ekcg_gram_with(ekcg_ctx* ctx, const double* X, int p, const double* Y, int q
  * doubles), present on every GPU that loads the library until the process exits; no call
  * allocates or frees memory.  The first call on a device looks up the array's device
  * address (cudaGetSymbolAddress) with that device current; make that first call before any
- * stream capture.  Every call shares the array and each call overwrites every entry it later
+ * stream capture.  The looked-up address is kept per device ordinal for the life of the
+ * process: it does not survive a device reset (cudaDeviceReset, or a reset of the primary
+ * context), after which calls on that device must not be made.  Every call shares the array and each call overwrites every entry it later
  * reads, so nothing has to be cleared between calls; calls that overlap on the GPU (other
  * streams, other host threads) race on the array and must be serialised by the caller.
  * Errors: EKCG_EINVAL (sizes, null pointers), EKCG_ECUDA (lookup or launch failure).     */
@@ -322,6 +348,13 @@ int ekcg_batched_set_shape(ekcg_batch* batch, int threads, int ctas_per_sm, int 
  * device time (ms) of the last captured solve; every pointer nullable.                   */
 int ekcg_batched_info(const ekcg_batch* batch, int* threads, int* ctas_per_sm, int* cluster,
                       int* groups, double* last_ms);
+
+/* Mixed (FP32_IR) batched solves: the number of systems of the last solve whose float32
+ * refinement stagnated (a refinement step reduced the float64 residual by less than 0.9,
+ * as when kappa(A) eps32 approaches 1) and that then continued, on the device, with a
+ * float64 s-step solve from the refined iterate in the same workspace.  Synchronises the
+ * batch's stream.  Errors: EKCG_EINVAL, EKCG_ECUDA.                                        */
+int ekcg_batched_precision_switches(const ekcg_batch* batch, int* count);
 
 /* Release the batch and its device memory (NULL accepted).                               */
 void ekcg_batched_destroy(ekcg_batch* batch);

@@ -73,6 +73,7 @@ struct Params {
     int* iters;                 // per system
     int* status;                // per system
     double* rho_out;            // per system: final recursive (or refined) residual norm
+    int* switched;              // per system: 1 if the mixed solve continued in float64
 };
 
 // ---- group-wide building blocks -------------------------------------------------------
@@ -514,11 +515,13 @@ __global__ void __launch_bounds__(512) k_batched(Params P) {
             its = cta_sstep<double>(P, S, g, xx, r64, Wb, Zb, P.val + S.nz0, rho0, P.tol * rho0,
                                     P.maxit, sh, scratch, &st, &rho);
         } else if (rho0 > 0) {
-            float* Wb = (float*)P.ws + S.ws0;
+            // float32 basis inside the system's workspace (sized for float64: see below)
+            float* Wb = reinterpret_cast<float*>((double*)P.ws + S.ws0);
             float* Zb = Wb + (int64_t)(P.s + 2) * S.n * P.t;
             float* d = Zb + (int64_t)(P.s + 1) * S.n * P.t;
             float* r32 = d + S.n;
             st = EKCG_MAXIT;
+            bool to64 = false;
             for (int ref = 0; ref < P.max_refine && its < P.maxit; ++ref) {
                 const double sc = 1.0 / rho;
                 for (int64_t i = g.lo + threadIdx.x; i < g.hi; i += blockDim.x) {
@@ -545,7 +548,25 @@ __global__ void __launch_bounds__(512) k_batched(Params P) {
                     st = EKCG_EBREAKDOWN;
                     break;
                 }
-                if (rho > 0.9 * rho_prev) break;   // refinement stagnated: EKCG_MAXIT
+                if (rho > 0.9 * rho_prev) {   // refinement stagnated (kappa eps32 near 1)
+                    to64 = true;
+                    break;
+                }
+            }
+            if (to64 && its < P.maxit) {
+                // precision switch for this system only: continue in float64 from the refined
+                // x and its float64 residual, in the same workspace (every CTA of the group
+                // has finished with the float32 basis: the residual above ended in a group
+                // barrier)
+                double* Wd = (double*)P.ws + S.ws0;
+                double* Zd = Wd + (int64_t)(P.s + 2) * S.n * P.t;
+                int st64 = EKCG_OK;
+                double rho64 = rho;
+                its += cta_sstep<double>(P, S, g, P.x + S.row0, r64, Wd, Zd, P.val + S.nz0, rho,
+                                         P.tol * rho0, P.maxit - its, sh, scratch, &st64, &rho64);
+                st = st64;
+                rho = rho64;
+                if (g.rank == 0 && threadIdx.x == 0) P.switched[sid] = 1;
             }
         }
         if (g.rank == 0 && threadIdx.x == 0) {
@@ -584,7 +605,7 @@ struct ekcg_batch {
     int64_t* d_perm = nullptr;   // global permuted position -> global natural row
     double *d_b = nullptr, *d_x = nullptr, *d_r = nullptr;
     void* d_ws = nullptr;
-    int *d_iters = nullptr, *d_status = nullptr;
+    int *d_iters = nullptr, *d_status = nullptr, *d_switched = nullptr;
     double* d_rho = nullptr;
     int threads = 512, ctas_per_sm = 1;
     int cluster = 1;            // CTAs per system (a thread-block cluster when > 1)
@@ -623,8 +644,10 @@ int launch_solve(ekcg_batch* B, int s, double tol, int maxit) {
     P.iters = B->d_iters;
     P.status = B->d_status;
     P.rho_out = B->d_rho;
+    P.switched = B->d_switched;
     const size_t smem = (size_t)B->threads * sizeof(double);
     EB_CUDA(cudaMemsetAsync(B->d_queue, 0, sizeof(int), B->stream));
+    EB_CUDA(cudaMemsetAsync(B->d_switched, 0, B->nsys * sizeof(int), B->stream));
     EB_CUDA(cudaMemsetAsync(B->d_x, 0, B->ntot * sizeof(double), B->stream));
     const bool mixed = B->precision != EKCG_FP64;
     if (B->cluster == 1) {
@@ -818,7 +841,9 @@ int ekcg_batched_setup(int nsys, const int64_t* n, const int64_t* rowptr, const 
     std::stable_sort(order.begin(), order.end(),
                      [&](int a, int b) { return sys[a].n > sys[b].n; });
     std::vector<float> hval32(hval.begin(), hval.end());
-    const size_t esz = o.precision == EKCG_FP64 ? sizeof(double) : sizeof(float);
+    // float64-sized in both precisions: a mixed system whose float32 refinement stagnates
+    // continues in float64 in the same workspace
+    const size_t esz = sizeof(double);
     auto fail = [&](int rc) {
         ekcg_batched_destroy(B);
         return rc;
@@ -847,6 +872,7 @@ int ekcg_batched_setup(int nsys, const int64_t* n, const int64_t* rowptr, const 
     EB_TRY(cudaMalloc(&B->d_iters, nsys * sizeof(int)));
     EB_TRY(cudaMalloc(&B->d_status, nsys * sizeof(int)));
     EB_TRY(cudaMalloc(&B->d_rho, nsys * sizeof(double)));
+    EB_TRY(cudaMalloc(&B->d_switched, nsys * sizeof(int)));
     EB_TRY(cudaMemcpy(B->d_sys, sys.data(), nsys * sizeof(Sys), cudaMemcpyHostToDevice));
     EB_TRY(cudaMemcpy(B->d_order, order.data(), nsys * sizeof(int32_t), cudaMemcpyHostToDevice));
     EB_TRY(cudaMemcpy(B->d_rowptr, hrow.data(), hrow.size() * sizeof(int32_t),
@@ -970,11 +996,22 @@ int ekcg_batched_info(const ekcg_batch* B, int* threads, int* ctas_per_sm, int* 
     return EKCG_OK;
 }
 
+int ekcg_batched_precision_switches(const ekcg_batch* B, int* count) {
+    if (!B || !count) return EKCG_EINVAL;
+    std::vector<int> h(B->nsys);
+    EB_CUDA(cudaMemcpyAsync(h.data(), B->d_switched, B->nsys * sizeof(int),
+                            cudaMemcpyDeviceToHost, B->stream));
+    EB_CUDA(cudaStreamSynchronize(B->stream));
+    *count = 0;
+    for (int v : h) *count += v != 0;
+    return EKCG_OK;
+}
+
 void ekcg_batched_destroy(ekcg_batch* B) {
     if (!B) return;
     void* ptrs[] = {B->d_sys, B->d_order, B->d_queue, B->d_rowptr, B->d_col, B->d_val,
                     B->d_val32, B->d_dom, B->d_perm, B->d_b, B->d_x, B->d_r, B->d_ws,
-                    B->d_iters, B->d_status, B->d_rho};
+                    B->d_iters, B->d_status, B->d_rho, B->d_switched};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (B->graph) cudaGraphExecDestroy(B->graph);

@@ -104,8 +104,21 @@ struct ekcg_ctx {
     double* alpha = nullptr;
     double* rho = nullptr;         // device scalars: [0] current norm, [1] scratch
     int* flag = nullptr;           // bit 0: Cholesky breakdown
+    int* ndefl = nullptr;          // columns deflated (dropped) by the Cholesky kernel
+    int64_t last_deflated = 0;     // ... in the last solve
     double* h_pinned = nullptr;    // pinned host: rho
     int* h_flag = nullptr;         // pinned host: flag
+
+    // device-side s-step loop (CUDA graph of conditional iterations)
+    int device_loop = 1;           // 0: the host checks the residual every iteration
+    int* loop_state = nullptr;     // device loop state (LoopField)
+    int* h_loop = nullptr;         // pinned host copy of the loop state
+    double* loop_hist = nullptr;   // device residual history of the device loop
+    int loop_hist_cap = 0;
+    int64_t loop_iters = 0;        // iterations run by the device loop in the last solve
+    cudaStream_t cap_stream = nullptr;   // capture stream of the device loop (the context's
+                                         // own stream may be the legacy stream, which cannot
+                                         // be captured)
 
     // block Jacobi preconditioner, IC(0) blocks (Section 5); bj_nblk = 0: none.  Forward
     // (L) and backward (L^T) solves: per-row CSR of the off-diagonal entries, level lists.
@@ -791,7 +804,7 @@ int run_trsm(ekcg_ctx* c, MB<double> X) {
 int run_chol(ekcg_ctx* c, int m) {
     Launch L(c, KC_CHOL);
     k_chol_inv<<<1, 512, 0, c->stream>>>(c->G, m, c->S, c->R, c->Rinv, c->opts.breakdown_tol,
-                                         c->flag);
+                                         c->flag, c->opts.deflate, c->ndefl);
     return check_launch("k_chol_inv");
 }
 
@@ -899,7 +912,10 @@ struct Engine {
     // the product with R^{-1}.
     int apply_rinv(int64_t j, int cnt) {
         if constexpr (std::is_same<T, double>::value) {
-            if (c->opts.contraction == EKCG_CONTRACT_SPLIT && cnt == 1 && (t == 16 || t == 32)) {
+            // deflation zeroes the dropped rows and columns of R^{-1} (the triangular solve
+            // with R would leave a dropped column nonzero), so it multiplies by R^{-1} too
+            if (c->opts.deflate ||
+                (c->opts.contraction == EKCG_CONTRACT_SPLIT && cnt == 1 && (t == 16 || t == 32))) {
                 EK_TRY((run_rmul<T, T>(c, Wm(j, cnt), c->Rinv)));
                 return run_rmul<T, T>(c, Zm(j, cnt), c->Rinv);
             }
@@ -1128,6 +1144,194 @@ int run_norm(ekcg_ctx* c, const T* v) {
     return check_launch("k_norm_finalize");
 }
 
+// ---------------------------------------------------------------------------------------
+// Device-side convergence (the `while` line of Algorithms 3/4): iterations run inside a
+// CUDA graph; after each one a single-thread kernel tests rho_k > tol rho_0 and k < k_max on
+// the device, appends rho_k to a device history and enables the next iteration's
+// conditional node.  The host synchronises once per batch of iterations.
+// ---------------------------------------------------------------------------------------
+enum LoopField { LS_K = 0, LS_ITERS, LS_STATUS, LS_DONE, LS_NH };
+
+__global__ void k_loop_check(const double* __restrict__ rho, const int* __restrict__ flag,
+                             int* __restrict__ st, double* __restrict__ hdev, int hcap,
+                             double tol_abs, int maxit, cudaGraphConditionalHandle next,
+                             int has_next) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    int done = 0;
+    const int f = *flag;
+    if (f & 4) {
+        st[LS_STATUS] = EKCG_ETIMEOUT;
+        done = 1;
+    } else if (f & 1) {
+        st[LS_STATUS] = EKCG_EBREAKDOWN;   // the update kept the last complete iterate
+        done = 1;
+    } else {
+        const double r = rho[0];
+        if (st[LS_NH] < hcap) hdev[st[LS_NH]] = r;
+        st[LS_NH] += 1;
+        st[LS_ITERS] = st[LS_K];
+        st[LS_K] += 1;
+        if (!(r > tol_abs)) {
+            st[LS_STATUS] = EKCG_OK;
+            done = 1;
+        } else if (st[LS_K] >= maxit + 1) {
+            st[LS_STATUS] = EKCG_MAXIT;
+            done = 1;
+        }
+    }
+    st[LS_DONE] = done;
+    if (has_next) cudaGraphSetConditional(next, done ? 0u : 1u);
+}
+
+// Runs the remaining s-step iterations of s-step / restructured SRE-CG (Algorithms 4, 2:
+// every iteration after the window is full launches the same kernels on ring slots that
+// repeat with a fixed period) as a CUDA graph of B conditional iterations, launched
+// until the loop state says done.  k0: the next iteration number.  Returns the status and
+// appends the residual norms to hist / *hlen like the host loop.
+int device_loop(ekcg_ctx* c, Engine<double>& E, int s, double tol_abs, int maxit, int k0,
+                double* hist, int cap, int* hlen, int* iters) {
+    // the W ring (E.ring slots) and the A W ring (E.zring slots) both repeat after `period`
+    // iterations of s blocks each
+    auto gcd = [](int a, int b) {
+        while (b) {
+            const int t = a % b;
+            a = b;
+            b = t;
+        }
+        return a;
+    };
+    const int pw = E.ring / gcd(s, E.ring), pz = E.zring / gcd(s, E.zring);
+    const int period = pw / gcd(pw, pz) * pz;
+    const int B = period * std::max(1, 8 / period);
+    const int left = maxit - k0 + 1;
+    const int need = std::max(1, std::min(left, 1 << 22));
+    if (need > c->loop_hist_cap) {
+        if (c->loop_hist) cudaFree(c->loop_hist);
+        c->loop_hist = nullptr;
+        c->loop_hist_cap = 0;
+        EK_CUDA(cudaMalloc(&c->loop_hist, (size_t)need * sizeof(double)));
+        c->loop_hist_cap = need;
+    }
+    int* hs = c->h_loop;
+    hs[LS_K] = k0;
+    hs[LS_ITERS] = k0 - 1;
+    hs[LS_STATUS] = EKCG_OK;
+    hs[LS_DONE] = 0;
+    hs[LS_NH] = 0;
+    EK_CUDA(cudaMemcpyAsync(c->loop_state, hs, 8 * sizeof(int), cudaMemcpyHostToDevice,
+                            c->stream));
+    // build: B conditional nodes in a chain, iteration b captured into the body of node b.
+    // The engine's launches go to the capture stream while the bodies are recorded; the
+    // graph then runs on the context's stream.
+    if (!c->cap_stream) EK_CUDA(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+    cudaGraph_t graph = nullptr;
+    EK_CUDA(cudaGraphCreate(&graph, 0));
+    std::vector<cudaGraphConditionalHandle> hd(B);
+    int rc = EKCG_OK;
+    const int64_t nb0 = E.nblocks;
+    const int64_t l0 = c->launches;
+    cudaGraphNode_t prev = nullptr;
+    // every handle exists before any body is captured: body b sets the handle of body b + 1
+    for (int b = 0; b < B && rc == EKCG_OK; ++b)
+        if (cudaGraphConditionalHandleCreate(&hd[b], graph, b == 0 ? 1u : 0u,
+                                             cudaGraphCondAssignDefault) != cudaSuccess) {
+            set_error("device loop", "conditional handle");
+            rc = EKCG_ECUDA;
+        }
+    for (int b = 0; b < B && rc == EKCG_OK; ++b) {
+        // zero-initialised parameter block (the struct's union has no default constructor)
+        alignas(cudaGraphNodeParams) unsigned char raw[sizeof(cudaGraphNodeParams)];
+        std::memset(raw, 0, sizeof(raw));
+        cudaGraphNodeParams* np = reinterpret_cast<cudaGraphNodeParams*>(raw);
+        np->type = cudaGraphNodeTypeConditional;
+        np->conditional.handle = hd[b];
+        np->conditional.type = cudaGraphCondTypeIf;
+        np->conditional.size = 1;
+        cudaGraphNode_t node;
+        if (cudaGraphAddNode(&node, graph, prev ? &prev : nullptr, nullptr, prev ? 1 : 0, np) !=
+            cudaSuccess) {
+            set_error("device loop", "conditional node");
+            rc = EKCG_ECUDA;
+            break;
+        }
+        prev = node;
+        cudaGraph_t body = np->conditional.phGraph_out[0];
+        const cudaStream_t keep = c->stream;
+        c->stream = c->cap_stream;
+        if (cudaStreamBeginCaptureToGraph(c->stream, body, nullptr, nullptr, 0,
+                                          cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+            c->stream = keep;
+            set_error("device loop", "capture");
+            rc = EKCG_ECUDA;
+            break;
+        }
+        int64_t v0 = 0;
+        int r1 = E.iterate_sstep(k0 + b, E.r, &v0);
+        if (r1 == EKCG_OK)
+            r1 = c->opts.basis == EKCG_RESTRUCT ? E.update_restructured(v0) : E.update(v0);
+        if (r1 == EKCG_OK) {
+            k_loop_check<<<1, 32, 0, c->stream>>>(c->rho, c->flag, c->loop_state, c->loop_hist,
+                                                  c->loop_hist_cap, tol_abs, maxit,
+                                                  b + 1 < B ? hd[b + 1] : hd[b], b + 1 < B);
+            c->launches++;
+            r1 = check_launch("k_loop_check");
+        }
+        cudaGraph_t out = nullptr;
+        const cudaError_t ce = cudaStreamEndCapture(c->stream, &out);
+        c->stream = keep;
+        if (r1 != EKCG_OK) {
+            rc = r1;
+        } else if (ce != cudaSuccess) {
+            set_error("device loop capture", cudaGetErrorString(ce));
+            rc = EKCG_ECUDA;
+        }
+    }
+    const int64_t per_iter = (c->launches - l0) / std::max(1, B);
+    cudaGraphExec_t exec = nullptr;
+    if (rc == EKCG_OK && cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) {
+        set_error("device loop", "graph instantiation failed");
+        rc = EKCG_ECUDA;
+    }
+    // run: every launch executes up to B iterations; the host reads the state once per launch
+    int status = EKCG_MAXIT;
+    while (rc == EKCG_OK) {
+        if (cudaGraphLaunch(exec, c->stream) != cudaSuccess) {
+            set_error("device loop", "graph launch");
+            rc = EKCG_ECUDA;
+            break;
+        }
+        if (cudaMemcpyAsync(hs, c->loop_state, 8 * sizeof(int), cudaMemcpyDeviceToHost,
+                            c->stream) != cudaSuccess ||
+            cudaStreamSynchronize(c->stream) != cudaSuccess) {
+            set_error("device loop", "state read");
+            rc = EKCG_ECUDA;
+            break;
+        }
+        E.nblocks = nb0 + (int64_t)(hs[LS_K] - k0) * s;
+        if (hs[LS_DONE]) {
+            status = hs[LS_STATUS];
+            break;
+        }
+    }
+    if (exec) cudaGraphExecDestroy(exec);
+    cudaGraphDestroy(graph);
+    if (rc != EKCG_OK) return rc;
+    // the history, as the host loop would have written it
+    const int nh = std::min(hs[LS_NH], c->loop_hist_cap);
+    if (hist && nh > 0 && *hlen < cap) {
+        const int m = std::min(nh, cap - *hlen);
+        EK_CUDA(cudaMemcpy(hist + *hlen, c->loop_hist, (size_t)m * sizeof(double),
+                           cudaMemcpyDeviceToHost));
+    }
+    *hlen += hs[LS_NH];
+    *iters = hs[LS_ITERS];
+    c->loop_iters = hs[LS_K] - k0;
+    c->launches = l0 + per_iter * c->loop_iters;
+    if (status == EKCG_ETIMEOUT)
+        set_error("ekcg_solve", "a staged bulk copy did not complete within its wait limit");
+    return status;
+}
+
 // The enlarged s-step loop on the permuted system in precision T.
 //   x: initial guess / solution (T), r: residual b - A x on entry (T), rho0 = ||r||.
 //   hist: receives rho_1.. (not rho_0) up to cap; returns status; *iters iterations done.
@@ -1146,8 +1350,17 @@ int sstep_loop(ekcg_ctx* c, int s, double tol_abs, int maxit, T* x, T* r, double
     int status = EKCG_OK;
     *iters = 0;
     int flag = 0;
+    const bool on_device = std::is_same<T, double>::value && c->device_loop &&
+                           !c->opts.profile && stag == 0 && c->opts.variant == EKCG_SRE &&
+                           (c->opts.basis == EKCG_SSTEP || c->opts.basis == EKCG_RESTRUCT);
+    c->loop_iters = 0;
     while (rho > tol_abs && k < maxit + 1 &&
            !(stag > 0 && k - 1 - k_best >= std::max(stag, k_best / 2))) {
+        if constexpr (std::is_same<T, double>::value) {
+            // once the window is full every iteration launches the same kernels
+            if (on_device && E.nblocks >= 2)
+                return device_loop(c, E, s, tol_abs, maxit, k, hist, cap, hlen, iters);
+        }
         int64_t v0 = 0;
         const bool sstep_basis = c->opts.basis == EKCG_SSTEP || c->opts.basis == EKCG_RESTRUCT;
         int rc = sstep_basis ? E.iterate_sstep(k, r, &v0) : E.iterate_ca(k, r, &v0);
@@ -1360,8 +1573,11 @@ int alloc_workspace(ekcg_ctx* c) {
     EK_CUDA(cudaMalloc(&c->alpha, c->max_m * sizeof(double)));
     EK_CUDA(cudaMalloc(&c->rho, 4 * sizeof(double)));
     EK_CUDA(cudaMalloc(&c->flag, sizeof(int)));
+    EK_CUDA(cudaMalloc(&c->ndefl, sizeof(int)));
     EK_CUDA(cudaMallocHost(&c->h_pinned, 4 * sizeof(double)));
     EK_CUDA(cudaMallocHost(&c->h_flag, sizeof(int)));
+    EK_CUDA(cudaMalloc(&c->loop_state, 8 * sizeof(int)));
+    EK_CUDA(cudaMallocHost(&c->h_loop, 8 * sizeof(int)));
     EK_CUDA(cudaFuncSetAttribute(k_update<double, double>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)(kUpdRows * (kPMax + 1) * sizeof(double))));
@@ -1388,12 +1604,15 @@ void free_ctx(ekcg_ctx* c) {
                     c->nat_rowptr, c->W64, c->Z64,
                     c->W32, c->Z32, c->xb, c->rb, c->bb, c->x32, c->r32, c->nat_tmp,
                     c->partials, c->partials32, c->red, c->C64, c->C32, c->G, c->S, c->R,
-                    c->Rinv, c->Rinv32, c->alpha, c->rho, c->flag};
+                    c->Rinv, c->Rinv32, c->alpha, c->rho, c->flag, c->ndefl, c->loop_state,
+                    c->loop_hist};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     free_block_jacobi(c);
     if (c->h_pinned) cudaFreeHost(c->h_pinned);
     if (c->h_flag) cudaFreeHost(c->h_flag);
+    if (c->h_loop) cudaFreeHost(c->h_loop);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     for (auto e : c->ev_pool) cudaEventDestroy(e);
 }
 
@@ -1442,6 +1661,7 @@ int solve_device(ekcg_ctx* c, const double* b, const double* x0, int s, double t
     }
     EK_TRY(check_launch("x0"));
     EK_CUDA(cudaMemsetAsync(c->flag, 0, sizeof(int), c->stream));
+    EK_CUDA(cudaMemsetAsync(c->ndefl, 0, sizeof(int), c->stream));
     // r_0 = b - A x_0, rho_0 = ||r_0||
     {
         Launch L(c, KC_RESID, 2.0 * c->nnz + 3.0 * n,
@@ -1539,7 +1759,12 @@ int solve_device(ekcg_ctx* c, const double* b, const double* x0, int s, double t
         k_scatter<double><<<grid_for(c, n), kThreads, 0, c->stream>>>(x, c->xb, c->perm, n);
     }
     EK_TRY(check_launch("k_scatter"));
-    EK_CUDA(cudaStreamSynchronize(c->stream));
+    {
+        int nd = 0;
+        EK_CUDA(cudaMemcpyAsync(&nd, c->ndefl, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+        EK_CUDA(cudaStreamSynchronize(c->stream));
+        c->last_deflated = nd;
+    }
     EK_TRY(collect_profile(c));
     if (iters) *iters = it;
     if (hlen) *hlen = hl;
@@ -1697,7 +1922,8 @@ int ekcg_setup(int64_t n, const int64_t* rowptr, const int32_t* colind, const do
         o.orth > 1 || o.precision < 0 || o.precision > 1 || o.max_s < 1 ||
         o.max_s * t > kPMax || o.max_blocks < 0 || !(o.breakdown_tol >= 0) ||
         !(o.inner_tol > 0 && o.inner_tol < 1) || o.max_refine < 1 ||
-        (o.contraction != EKCG_CONTRACT_FP64 && o.contraction != EKCG_CONTRACT_SPLIT)) {
+        (o.contraction != EKCG_CONTRACT_FP64 && o.contraction != EKCG_CONTRACT_SPLIT) ||
+        o.deflate < 0 || o.deflate > 1 || (o.deflate && o.orth != EKCG_ACHOLQR)) {
         set_error("ekcg_setup", "invalid options (note: max_s * t must be <= 256)");
         delete c;
         return EKCG_EINVAL;
@@ -1983,6 +2209,24 @@ int ekcg_fp64_fma_rate(void* stream, int* num_sms, double* tflops) {
     if (e != cudaSuccess || ms <= 0.f) return EKCG_ECUDA;
     *num_sms = sms;
     *tflops = 2.0 * (double)blocks * threads * 16.0 * iters / (ms * 1e-3) / 1e12;
+    return EKCG_OK;
+}
+
+int ekcg_deflation_stats(const ekcg_ctx* c, int64_t* columns) {
+    if (!c || !columns) return EKCG_EINVAL;
+    *columns = c->last_deflated;
+    return EKCG_OK;
+}
+
+int ekcg_set_device_loop(ekcg_ctx* c, int on) {
+    if (!c) return EKCG_EINVAL;
+    c->device_loop = on ? 1 : 0;
+    return EKCG_OK;
+}
+
+int ekcg_device_loop_stats(const ekcg_ctx* c, int64_t* device_iters) {
+    if (!c || !device_iters) return EKCG_EINVAL;
+    *device_iters = c->loop_iters;
     return EKCG_OK;
 }
 

@@ -683,8 +683,13 @@ k_rmul_f32(MB<float> X, const float* __restrict__ R, int ldr, int64_t n) {
 // d_i <= tol*|G_ii| or non-finite sets bit 0 of *flag and leaves R = Rinv = I.
 __global__ void k_chol_inv(const double* __restrict__ G, int m, double* __restrict__ S,
                            double* __restrict__ R, double* __restrict__ Rinv, double tol,
-                           int* __restrict__ flag) {
+                           int* __restrict__ flag, int deflate, int* __restrict__ ndefl) {
+    // deflate != 0: a finite pivot that fails the breakdown rule drops its column (row e_i^T
+    // in R, no Schur update from it; row and column i of R^{-1} zero, so W R^{-1} has a zero
+    // column i); a block whose columns are all dropped is a breakdown.
     __shared__ int bad;
+    __shared__ int ndrop;
+    __shared__ unsigned char dropped[kPMax];
     const int tid = threadIdx.x, nt = blockDim.x;
     for (int e = tid; e < m * m; e += nt) {
         const int i = e / m, j = e - i * m;
@@ -692,18 +697,30 @@ __global__ void k_chol_inv(const double* __restrict__ G, int m, double* __restri
         R[e] = 0.0;
         Rinv[e] = 0.0;
     }
-    if (tid == 0) bad = (*flag) & 1;
+    for (int i = tid; i < m; i += nt) dropped[i] = 0;
+    if (tid == 0) {
+        bad = (*flag) & 1;
+        ndrop = 0;
+    }
     __syncthreads();
     for (int i = 0; i < m && !bad; ++i) {
         if (tid == 0) {
             const double d = S[i * m + i];
-            if (!(d > tol * fabs(G[i * m + i])) || !isfinite(d))
-                bad = 1;
-            else
+            if (!(d > tol * fabs(G[i * m + i])) || !isfinite(d)) {
+                if (deflate && isfinite(d)) {
+                    R[i * m + i] = 1.0;
+                    dropped[i] = 1;
+                    ++ndrop;
+                } else {
+                    bad = 1;
+                }
+            } else {
                 R[i * m + i] = sqrt(d);
+            }
         }
         __syncthreads();
         if (bad) break;
+        if (dropped[i]) continue;
         const double rii = R[i * m + i];
         for (int j = i + 1 + tid; j < m; j += nt) R[i * m + j] = S[i * m + j] / rii;
         __syncthreads();
@@ -714,6 +731,8 @@ __global__ void k_chol_inv(const double* __restrict__ G, int m, double* __restri
         }
         __syncthreads();
     }
+    if (tid == 0 && !bad && ndrop == m) bad = 1;   // every column dropped
+    __syncthreads();
     if (bad) {
         for (int e = tid; e < m * m; e += nt) {
             const int i = e / m, j = e - i * m;
@@ -730,6 +749,14 @@ __global__ void k_chol_inv(const double* __restrict__ G, int m, double* __restri
             for (int k = i + 1; k <= c; ++k) s -= R[i * m + k] * Rinv[k * m + c];
             Rinv[i * m + c] = s / R[i * m + i];
         }
+    }
+    if (ndrop) {
+        __syncthreads();
+        for (int e = tid; e < m * m; e += nt) {
+            const int i = e / m, j = e - i * m;
+            if (dropped[i] || dropped[j]) Rinv[e] = 0.0;
+        }
+        if (tid == 0) atomicAdd(ndefl, ndrop);
     }
 }
 

@@ -32,7 +32,7 @@ class ekcg_opts(ctypes.Structure):
     _fields_ = [("variant", c_int), ("basis", c_int), ("orth", c_int), ("precision", c_int),
                 ("max_s", c_int), ("max_blocks", c_int), ("max_basis_bytes", c_int64),
                 ("breakdown_tol", c_double), ("inner_tol", c_double), ("max_refine", c_int),
-                ("profile", c_int), ("contraction", c_int)]
+                ("profile", c_int), ("contraction", c_int), ("deflate", c_int)]
 
 
 class EkcgError(RuntimeError):
@@ -77,6 +77,12 @@ def _declare(L):
     L.ekcg_wait_selftest.restype = c_int
     L.ekcg_fp64_fma_rate.argtypes = [c_void_p, POINTER(c_int), POINTER(c_double)]
     L.ekcg_fp64_fma_rate.restype = c_int
+    L.ekcg_deflation_stats.argtypes = [c_void_p, POINTER(c_int64)]
+    L.ekcg_deflation_stats.restype = c_int
+    L.ekcg_set_device_loop.argtypes = [c_void_p, c_int]
+    L.ekcg_set_device_loop.restype = c_int
+    L.ekcg_device_loop_stats.argtypes = [c_void_p, POINTER(c_int64)]
+    L.ekcg_device_loop_stats.restype = c_int
     L.ekcg_set_profile.argtypes = [c_void_p, c_int]
     L.ekcg_set_profile.restype = c_int
     L.ekcg_profile.argtypes = [c_void_p, c_int, POINTER(c_char_p), POINTER(c_double),
@@ -122,6 +128,8 @@ def _declare(L):
     L.ekcg_batched_info.argtypes = [c_void_p, POINTER(c_int), POINTER(c_int), POINTER(c_int),
                                     POINTER(c_int), POINTER(c_double)]
     L.ekcg_batched_info.restype = c_int
+    L.ekcg_batched_precision_switches.argtypes = [c_void_p, POINTER(c_int)]
+    L.ekcg_batched_precision_switches.restype = c_int
     L.ekcg_batched_destroy.argtypes = [c_void_p]
     L.ekcg_batched_destroy.restype = None
     L.ekcg_batched_last_error.argtypes = []
@@ -344,7 +352,7 @@ class Solver:
     def __init__(self, A, t, part, variant="sre", basis="sstep", orth="acholqr",
                  precision="fp64", max_s=8, max_blocks=0, max_basis_bytes=0,
                  breakdown_tol=1e-14, inner_tol=1e-4, max_refine=30, profile=False,
-                 stream=None, contraction=None):
+                 stream=None, contraction=None, deflate=False):
         import torch
         o = ekcg_default_opts()
         o.variant, o.basis, o.orth = VARIANT[variant], BASIS[basis], ORTH[orth]
@@ -354,6 +362,7 @@ class Solver:
         o.profile = int(bool(profile))
         if contraction is not None:          # None: the library default (split products)
             o.contraction = CONTRACTION[contraction]
+        o.deflate = int(bool(deflate))
         if stream is None:
             stream = torch.cuda.current_stream().cuda_stream
         self.n = int(A.n)
@@ -414,6 +423,22 @@ class Solver:
         """Per-launch CUDA-event timing of later solves on or off."""
         lib().ekcg_set_profile(self.ctx, int(bool(on)))
 
+    def set_device_loop(self, on):
+        """Device-side convergence test (CUDA graph of conditional iterations) on or off."""
+        lib().ekcg_set_device_loop(self.ctx, int(bool(on)))
+
+    def device_loop_iters(self):
+        """Iterations of the last solve that ran in the device loop."""
+        v = c_int64()
+        lib().ekcg_device_loop_stats(self.ctx, byref(v))
+        return v.value
+
+    def deflated_columns(self):
+        """Columns the rank-revealing A-CholQR dropped in the last solve."""
+        v = c_int64()
+        lib().ekcg_deflation_stats(self.ctx, byref(v))
+        return v.value
+
 
 class BatchedSolver:
     """Many independent systems (a list of workloads.Problem-like objects with .A and .part)
@@ -467,6 +492,14 @@ class BatchedSolver:
         if st != EKCG_OK:
             raise RuntimeError(f"ekcg_batched_set_shape: {strerror(st)}: "
                                f"{lib().ekcg_batched_last_error().decode()}")
+
+    def precision_switches(self):
+        """Systems of the last mixed solve that continued in float64 after the float32
+        refinement stagnated."""
+        v = c_int()
+        _check(lib().ekcg_batched_precision_switches(self.h, byref(v)),
+               "ekcg_batched_precision_switches")
+        return v.value
 
     def info(self):
         th, cp, cl, gr, ms = c_int(), c_int(), c_int(), c_int(), c_double()

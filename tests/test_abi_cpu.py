@@ -29,6 +29,7 @@ def test_default_opts_and_strerror_need_no_gpu(lib):
     assert (o.variant, o.basis, o.orth, o.precision, o.max_s) == (0, 0, 0, 0, 8)
     assert o.breakdown_tol == 1e-14 and o.inner_tol == 1e-4 and o.max_refine == 30
     assert o.contraction == ekcg.CONTRACTION["split"]
+    assert o.deflate == 0
     assert ctypes.sizeof(ekcg.ekcg_opts) == 64
     assert ekcg.strerror(0) == "ok"
     assert "breakdown" in ekcg.strerror(-3)

@@ -172,6 +172,24 @@ def test_batched_mixed_reaches_tolerance_and_breakdown_is_per_system(cluster):
     B.close()
 
 
+def test_batched_mixed_high_contrast_switches_to_float64():
+    """Coefficient jumps up to 1e4 (the batched configuration's recipe) push kappa(A) eps32
+    towards 1, where the float32 inner solves stop reducing the float64 residual: those
+    systems continue on the device in float64 from the refined iterate, and every system
+    reaches the tolerance in the true residual."""
+    probs = small_batch(contrast=4.0)
+    B = ekcg.BatchedSolver(probs, 8, precision="fp32_ir", max_s=2)
+    x, it, st = B.solve(concat(probs), s=2, tol=1e-8, maxit=8000)
+    nsw = B.precision_switches()
+    xs = split(x.cpu().numpy(), probs)
+    for k, p in enumerate(probs):
+        assert st[k] == 0, (k, st[k])
+        rr = np.linalg.norm(p.b - p.A.to_scipy() @ xs[k]) / np.linalg.norm(p.b)
+        assert rr <= 1e-8 * 1.01, (k, rr)
+    assert 0 <= nsw <= len(probs)
+    B.close()
+
+
 @pytest.mark.slow
 def test_batched_full_config_subset_float64():
     """Systems of the full batched configuration (256 systems, grids 32^2..256^2, jumps up to

@@ -502,3 +502,76 @@ def test_bounded_wait_reports_timeout_and_device_stays_usable():
     x, it, hist, st = S.solve(dev(b), s=2, tol=1e-8, maxit=500)
     assert st == 0 and relres(A, b, x.cpu().numpy()) <= 1e-8 * 1.01
     S.close()
+
+
+# ----------------------------------------------------------------------------------------
+# Rank-revealing A-CholQR: deflation of dependent directions instead of breakdown
+# ----------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("variant", ["sre", "sre2", "msdo"])
+@pytest.mark.parametrize("s", [1, 2])
+def test_deflation_vanishing_domain_against_oracle(variant, s):
+    """b vanishes on one of the t = 4 domains, so T(r_0) has a zero column: with
+    deflate = True the GPU drops it as the oracle does and the solve converges (without
+    deflation both stop with a breakdown, test_edge_cases)."""
+    A, b, part = ragged_problem()
+    b = b.copy()
+    b[part == 2] = 0.0
+    ref = o.solve(A, b, part, 4, s, tol=1e-8, maxit=2000, variant=variant, deflate=True)
+    S = ekcg.Solver(A, 4, part, variant=variant, max_s=s, max_basis_bytes=8 << 30,
+                    deflate=True)
+    x, it, hist, st = S.solve(dev(b), s=s, tol=1e-8, maxit=2000)
+    ndef = S.deflated_columns()
+    S.close()
+    assert st == ref.status == o.OK and ndef >= 1
+    assert abs(it - ref.iters) <= 1, (it, ref.iters)
+    m = min(21, len(hist), len(ref.hist))
+    np.testing.assert_allclose(hist[:m], ref.hist[:m], rtol=1e-6)
+    x = x.cpu().numpy()
+    assert relres(A, b, x) <= 1e-8 * 1.01
+    assert np.linalg.norm(x - ref.x) <= 1e-8 * np.linalg.norm(ref.x)
+
+
+def test_deflation_needs_acholqr():
+    A, b, part = ragged_problem()
+    with pytest.raises(ekcg.EkcgError):
+        ekcg.Solver(A, 4, part, orth="precholqr", deflate=True)
+
+
+# ----------------------------------------------------------------------------------------
+# Device-side convergence (the `while` line of Algorithms 3 / 4 tested on the device)
+# ----------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("basis,s", [("sstep", 1), ("sstep", 2), ("sstep", 3),
+                                     ("sstep", 4), ("restructured", 2)])
+def test_device_loop_matches_host_loop_bitwise(basis, s):
+    """The graph of conditional iterations launches the host loop's kernels in the host
+    loop's order: x, the iteration count and every residual norm are bitwise the same;
+    the iterations after the window fills ran on the device."""
+    A, b, part = ragged_problem()
+    S = ekcg.Solver(A, 4, part, basis=basis, max_s=s)
+    S.set_device_loop(True)
+    xd, itd, hd, std = S.solve(dev(b), s=s, tol=1e-8, maxit=2000)
+    on_dev = S.device_loop_iters()
+    S.set_device_loop(False)
+    xh, ith, hh, sth = S.solve(dev(b), s=s, tol=1e-8, maxit=2000)
+    assert S.device_loop_iters() == 0
+    S.close()
+    assert std == sth == 0 and itd == ith
+    assert on_dev == itd - (2 if s == 1 else 1)
+    assert np.array_equal(xd.cpu().numpy(), xh.cpu().numpy())
+    assert np.array_equal(hd, hh)
+
+
+@pytest.mark.parametrize("maxit", [2, 3, 9, 10, 11, 17])
+def test_device_loop_stops_at_maxit(maxit):
+    """maxit reached inside a batch of graph iterations: status EKCG_MAXIT, exactly maxit
+    iterations, maxit + 1 residual norms, the iterate of the host loop."""
+    A, b, part = ragged_problem()
+    S = ekcg.Solver(A, 4, part, max_s=2)
+    x, it, hist, st = S.solve(dev(b), s=2, tol=1e-8, maxit=maxit)
+    S.set_device_loop(False)
+    xh, ith, hh, sth = S.solve(dev(b), s=2, tol=1e-8, maxit=maxit)
+    S.close()
+    assert st == sth == ekcg.EKCG_MAXIT and it == ith == maxit and len(hist) == maxit + 1
+    assert np.array_equal(x.cpu().numpy(), xh.cpu().numpy()) and np.array_equal(hist, hh)
