@@ -2,13 +2,21 @@
 //
 // OUT = Y + alpha X C for the CGS updates (X: the window blocks, P = nb * Q columns) and,
 // with X = OUT, beta off and C = R^{-1}, the in-place A-CholQR product W <- W R^{-1}.  A
-// persistent CTA walks row tiles of TR rows.  One thread issues, per tile, one
-// cp.async.bulk copy per block of X (a tile of a row-major n x Q block is one contiguous
-// run of TR * Q floats) and one for Y, all completing on the stage's mbarrier; three
-// stages keep two tiles in flight while the CTA computes the third.  Every thread then
-// computes 4 rows x 4 columns of the tile from shared memory (C sits in shared memory for
-// the whole launch), reading each X value once per 4 output columns.  The sum over k runs
-// in increasing k with one fused multiply-add per term, as in the unstaged kernel.
+// persistent CTA walks row tiles of TR rows.  One thread issues, per tile, cp.async.bulk
+// copies of the tile's rows of every block of X and of Y (a run of rows of a row-major
+// n x Q block is contiguous), all completing on the stage's mbarrier; three stages keep two
+// tiles in flight while the CTA computes the third.  Every thread then computes 4 rows x 4
+// columns of the tile from shared memory (C sits in shared memory for the whole launch),
+// reading each X value once per 4 output columns.  The sum over k runs in increasing k with
+// one fused multiply-add per term, as in the unstaged kernel.
+//
+// Bank layout: a warp's lanes are kCG column groups x kG row groups, and the kG row groups
+// read the same column of different rows at once.  Rows are 64 or 128 bytes long, so rows of
+// one contiguous tile would all start in the same banks (a kG-way conflict on every X load).
+// Each block's tile is therefore copied as kG sub-tiles of kSub rows, row group g taking its
+// rows from sub-tile g, and sub-tile j is placed 16 j bytes further into shared memory than
+// a dense layout would put it: the row groups' reads then fall into distinct 16-byte bank
+// groups.
 //
 // Requirements (checked by the host before it picks this kernel): every block base and the
 // slot stride 16-byte aligned, X.w == Q, Y and OUT single blocks, X not aliasing OUT unless
@@ -93,11 +101,13 @@ __global__ void k_wait_selftest(long long limit, int* err) {
 
 template <int P, int Q>
 struct Shape {
-    static_assert(Q % 4 == 0 && P % Q == 0 && Q <= 32 && P <= 64, "bulk update shape");
+    static_assert((Q == 16 || Q == 32) && P % Q == 0 && P <= 64, "bulk update shape");
     static constexpr int kCG = Q / 4;                    // float4 column groups
+    static constexpr int kG = 32 / kCG;                  // row groups per warp
     static constexpr int kTR = 4 * kThreads / kCG;       // rows per tile (4 per thread)
-    static constexpr int kXF = kTR * P;                  // X floats per stage
-    static constexpr int kSF = kXF + kTR * Q;            // floats per stage (X, then Y)
+    static constexpr int kSub = kTR / kG;                // rows per sub-tile (4 per warp)
+    static constexpr int kSubF = kSub * Q + 4;           // floats per sub-tile, with the skew
+    static constexpr int kSF = (P / Q + 1) * kG * kSubF; // floats per stage (X blocks, Y)
     static constexpr size_t kSmem = (size_t)(P * Q + kStages * kSF) * sizeof(float);
 };
 
@@ -107,7 +117,7 @@ k_update_bulk_f32(MB<const float> X, const float* __restrict__ C, int ldc, int c
                   MB<const float> Y, MB<float> OUT, int64_t n, int beta_on, float alpha,
                   int* err) {
     using S = Shape<P, Q>;
-    constexpr int NB = P / Q, TR = S::kTR;
+    constexpr int NB = P / Q, TR = S::kTR, G = S::kG, SUB = S::kSub;
     extern __shared__ __align__(128) float sm[];
     __shared__ __align__(8) uint64_t full[kStages];
     float* cs = sm;                         // C: P x Q
@@ -120,11 +130,19 @@ k_update_bulk_f32(MB<const float> X, const float* __restrict__ C, int ldc, int c
         const int64_t row0 = tile * TR;
         const int rows = (int)((n - row0) < TR ? (n - row0) : TR);
         float* xs = stage0 + st * S::kSF;
-        const uint32_t blk_bytes = (uint32_t)rows * Q * sizeof(float);
-        mbar_expect_tx(&full[st], blk_bytes * (NB + (beta_on ? 1 : 0)));
+        mbar_expect_tx(&full[st], (uint32_t)rows * Q * sizeof(float) * (NB + (beta_on ? 1 : 0)));
+        for (int g = 0; g < G && g * SUB < rows; ++g) {
+            const int r0 = g * SUB;
+            const int nr = rows - r0 < SUB ? rows - r0 : SUB;
+            const uint32_t bytes = (uint32_t)nr * Q * sizeof(float);
 #pragma unroll
-        for (int b = 0; b < NB; ++b) bulk_g2s(xs + b * TR * Q, X.blk(b) + row0 * Q, blk_bytes, &full[st]);
-        if (beta_on) bulk_g2s(xs + S::kXF, Y.blk(0) + row0 * Q, blk_bytes, &full[st]);
+            for (int b = 0; b < NB; ++b)
+                bulk_g2s(xs + (b * G + g) * S::kSubF, X.blk(b) + (row0 + r0) * Q, bytes,
+                         &full[st]);
+            if (beta_on)
+                bulk_g2s(xs + (NB * G + g) * S::kSubF, Y.blk(0) + (row0 + r0) * Q, bytes,
+                         &full[st]);
+        }
     };
 
     if (tid == 0) {
@@ -144,7 +162,10 @@ k_update_bulk_f32(MB<const float> X, const float* __restrict__ C, int ldc, int c
         for (int s = 0; s < kStages && blockIdx.x + s * step < ntile; ++s) ++c;
         issued = c;
     }
-    const int cg = tid % S::kCG, rg = tid / S::kCG;
+    // lane = (row group g, column group cg); thread rows g * SUB + 4 warp + i, i < 4
+    const int lane = tid & 31, warp = tid >> 5;
+    const int cg = lane % S::kCG, g = lane / S::kCG;
+    const int rloc = 4 * warp;             // first row of this thread within its sub-tile
     float* out = OUT.blk(0);
     int64_t it = 0;
     for (int64_t tile = blockIdx.x; tile < ntile; tile += step, ++it) {
@@ -159,8 +180,8 @@ k_update_bulk_f32(MB<const float> X, const float* __restrict__ C, int ldc, int c
             __syncthreads();
             return;
         }
-        const float* xs = stage0 + st * S::kSF;
-        const float* ys = xs + S::kXF;
+        const float* xs = stage0 + st * S::kSF + g * S::kSubF;   // this row group's sub-tiles
+        const float* ys = stage0 + st * S::kSF + (NB * G + g) * S::kSubF;
         const int64_t row0 = tile * TR;
         float4 acc[4];
 #pragma unroll
@@ -171,7 +192,7 @@ k_update_bulk_f32(MB<const float> X, const float* __restrict__ C, int ldc, int c
             float4 xv[4];
 #pragma unroll
             for (int i = 0; i < 4; ++i)
-                xv[i] = *reinterpret_cast<const float4*>(xs + b * TR * Q + (rg * 4 + i) * Q + kk);
+                xv[i] = *reinterpret_cast<const float4*>(xs + b * G * S::kSubF + (rloc + i) * Q + kk);
             float4 c4[4];
 #pragma unroll
             for (int j = 0; j < 4; ++j)
@@ -191,10 +212,10 @@ k_update_bulk_f32(MB<const float> X, const float* __restrict__ C, int ldc, int c
         const int rows = (int)((n - row0) < TR ? (n - row0) : TR);
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
-            const int r = rg * 4 + i;
+            const int r = g * SUB + rloc + i;
             if (r < rows) {
                 float4 y = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (beta_on) y = *reinterpret_cast<const float4*>(ys + r * Q + cg * 4);
+                if (beta_on) y = *reinterpret_cast<const float4*>(ys + (rloc + i) * Q + cg * 4);
                 float4 o;
                 o.x = y.x + alpha * acc[i].x;
                 o.y = y.y + alpha * acc[i].y;

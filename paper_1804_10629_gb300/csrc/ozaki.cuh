@@ -564,12 +564,23 @@ k_oz_update(MB<const double> X, const double* __restrict__ C, MB<const double> Y
 
 // ---- the Gram product ---------------------------------------------------------------
 // C = X^T Y over the n rows (CGS coefficients Q^T (A W), the A-CholQR Gram W^T (A W)):
-// X n x P (P <= 64, padded to the MMA's M = 64), Y n x Q (Q = 16 or 32).  The contraction
-// runs over rows, in tiles of 64 rows: every column of X and of Y is scaled by its binade
-// over the tile (e_p, f_q), so a tile's nine groups are exact in fp32 (<= 9 pairs x 64
-// rows x 127^2 < 2^24), and the epilogue adds the tile's (V >> 14) 2^{e_p + f_q - 2100} into a
-// float64 accumulator per output held in registers across the CTA's tiles.  Each CTA writes
-// its P x Q partial sum; k_gram_reduce adds the partials in CTA order.
+// X n x P (P <= 64), Y n x Q (Q = 16 or 32).  The contraction runs over rows, in tiles of 64
+// rows: every column of X and of Y is scaled by its binade over the tile (e_p, f_q), and
+// the epilogue adds the tile's (V >> 14) 2^{e_p + f_q - 2100} into a float64 accumulator
+// per output held in registers across the CTA's tiles.  Each CTA writes its P x Q partial
+// sum; k_gram_reduce adds the partials in CTA order.
+//
+// Slice pairs in M: the A operand of one MMA holds two X slices, a (rows 0-63, X column p
+// in row p) and a + 1 (rows 64-127), so every MMA runs at M = 128.  The MMA of the pair
+// (a, a + 1), a odd, multiplies by the Y slices 1 .. 10 - a stacked along N and starts at
+// the accumulator columns of group a + 1: tensor-memory lanes 0-63 receive the pairs (a, b)
+// in the columns of group a + b, lanes 64-127 the pairs (a + 1, b) in the columns of group
+// a + b as well, that is group (a + 1 + b) - 1.  So column block j holds group j + 2 in the
+// upper lanes and group j + 3 in the lower lanes (block 8 of the lower lanes, group 11, is
+// beyond the 45 pairs and not read).  A group of one half holds at most five pairs, so its
+// fp32 sum stays exact (5 x 64 rows x 127^2 < 2^24).  Five MMAs per K-step (slice 10 is
+// zero) instead of nine at M = 64.
+//
 //   warp 7     (producer): one thread copies the tile's rows of every X block and of Y
 //              (contiguous runs of 64 x w doubles) into one of two raw shared buffers with
 //              bulk copies completing on an mbarrier, one tile ahead of the slicers;
@@ -577,31 +588,37 @@ k_oz_update(MB<const double> X, const double* __restrict__ C, MB<const double> Y
 //              warp = (column block, row parity); pass 1 takes the column binades of the
 //              tile from the raw buffer (a shared max over the two row parities), pass 2
 //              cuts 8 rows x 1 column per thread and K-step into the stage ring;
-//   warp 6     (MMA): per K-step one MMA per X slice a (M = 64, K = 16) against the Y
-//              slices 1 .. 10 - a stacked along N, into the columns of groups a + 1 .. 10;
-//   warps 8-11 (epilogue): M = 64 keeps rows 16 q' .. 16 q' + 15 of D in lanes 0-15 of lane
-//              quarter q', so lanes 0-15 of warp 8 + q' own the outputs p = 16 q' + lane.
+//   warp 6     (MMA): per K-step the five pair MMAs (M = 128, K = 16, N in pieces <= 256);
+//   warps 8-11 (epilogue): warp 8 + q reads lane quarter q, so the thread for output row
+//              p = 32 (q & 1) + lane holds the upper groups (q < 2) or the lower groups
+//              (q >= 2) of that row.  Each combines its groups into a 64-bit integer per
+//              column, releases the accumulator to the MMA warp, and exchanges half of the
+//              columns through shared memory with its partner (same row, other half), so
+//              that each thread converts and scales Q / 2 of the row's outputs.
 constexpr int kGramThreads = 12 * 32;
 constexpr int kGramMmaWarp = 6;
 constexpr int kGramProducerWarp = 7;
 constexpr int kGramEpiWarp0 = 8;
 constexpr int kGramRows = 64;        // rows per tile (binade scope, exact fp32 sums)
-constexpr int kGramStages = 4;
+constexpr int kGramStages = 3;
+constexpr int kPairs = (kSlices + 1) / 2;   // X slice pairs per K-step (the last one half zero)
 
 template <int P, int Q>
 struct GramShape {
     static_assert(P % 16 == 0 && P >= 16 && P <= 64, "P: multiple of 16, at most 64");
     static_assert(Q == 16 || Q == 32, "Q: 16 or 32");
-    static constexpr int kM = 64;
-    static constexpr int kSliceA = kM * kKS * 2;                   // 2 KB
+    static constexpr int kM = 128;                                 // MMA M (slice pair)
+    static constexpr int kPairA = kM * kKS * 2;                    // 4 KB: one slice pair
     static constexpr int kSliceB = Q * kKS * 2;
-    static constexpr int kStageBytes = kSlices * (kSliceA + kSliceB);
-    static constexpr int kOffB = kSlices * kSliceA;                // B inside a stage
+    static constexpr int kStageBytes = kPairs * kPairA + kSlices * kSliceB;
+    static constexpr int kOffB = kPairs * kPairA;                  // B inside a stage
     static constexpr int kRawX = kGramRows * P * 8;                // raw X tile, bytes
     static constexpr int kRawY = kGramRows * Q * 8;
     static constexpr int kOffRaw = kGramStages * kStageBytes;      // raw buffers after ring
-    static constexpr int kSmem = kOffRaw + 2 * (kRawX + kRawY) + 1024;
-    static constexpr int kLboA = (kM / 8) * 128;
+    static constexpr int kXch = 64 * (Q / 2) * 8;                  // one exchange direction
+    static constexpr int kOffXch = kOffRaw + 2 * (kRawX + kRawY);
+    static constexpr int kSmem = kOffXch + 2 * kXch + 1024;
+    static constexpr int kLboA = (kM / 8) * 128;                   // 2 KB
     static constexpr int kLboB = (kSlices * Q / 8) * 128;          // Y slices stacked in N
     static constexpr uint32_t kAcc = (uint32_t)(kGroups * Q);
     static constexpr int kSets = 2 * kAcc <= 512 ? 2 : 1;          // accumulator sets
@@ -610,6 +627,7 @@ struct GramShape {
     static constexpr int kNB = (kT + 31) / 32;                     // column blocks
     static constexpr int kSlicers = 2 * kNB;                       // slicer warps (<= 6)
     static constexpr int kKSteps = kGramRows / kKS;                // 4
+    static_assert(kSmem <= 232448, "shared memory");
 };
 
 // partials[cta * 4096 + p * Q + q] = this CTA's share of (X^T Y)[p, q]
@@ -618,6 +636,7 @@ __global__ void __launch_bounds__(kGramThreads, 1)
 k_oz_gram(MB<const double> X, MB<const double> Y, int64_t n, double* __restrict__ partials,
           int* err) {
     using S = GramShape<P, Q>;
+    constexpr int QH = Q / 2;
     extern __shared__ __align__(1024) unsigned char oz_raw[];
     unsigned char* sm = oz_raw + ((1024 - (bulk::smem_addr(oz_raw) & 1023)) & 1023);
     __shared__ __align__(8) uint64_t full[kGramStages], empty[kGramStages];
@@ -652,7 +671,7 @@ k_oz_gram(MB<const double> X, MB<const double> Y, int64_t n, double* __restrict_
         abort_flag = 0;
         bulk::fence_barrier_init();
     }
-    // the ring starts zeroed: rows p >= P of the A operand stay zero
+    // the ring starts zeroed: rows p >= P of each half and the half of slice 10 stay zero
     for (int e = tid * 16; e < kGramStages * S::kStageBytes; e += blockDim.x * 16)
         *reinterpret_cast<uint4*>(sm + e) = make_uint4(0u, 0u, 0u, 0u);
     fence_async_smem();
@@ -726,13 +745,7 @@ k_oz_gram(MB<const double> X, MB<const double> Y, int64_t n, double* __restrict_
                         ms[u] = sign_magic(neg);
                         undo[u] = sign_undo(neg);
                     }
-                    // X: slice a at a * kSliceA; Y: slice a is B rows a Q .. a Q + Q - 1
-                    unsigned char* dst =
-                        sm + slot * S::kStageBytes +
-                        (isx ? (par * (S::kM / 8) + (cc >> 3)) * 128
-                             : S::kOffB + (par * (kSlices * Q / 8) + (cc >> 3)) * 128) +
-                        (cc & 7) * 16;
-                    const int sstride = isx ? S::kSliceA : (Q / 8) * 128;
+                    unsigned char* st = sm + slot * S::kStageBytes;
 #pragma unroll
                     for (int a = 0; a < kSlices; ++a) {
                         uint4 v;
@@ -744,7 +757,14 @@ k_oz_gram(MB<const double> X, MB<const double> Y, int64_t n, double* __restrict_
                                         slice_bits(F[5], a, ms[5], undo[5]));
                         v.w = pack_bf16(slice_bits(F[6], a, ms[6], undo[6]),
                                         slice_bits(F[7], a, ms[7], undo[7]));
-                        *reinterpret_cast<uint4*>(dst + a * sstride) = v;
+                        // X: slice a (0-based) in pair a / 2, rows 64 (a % 2) + cc, K-group
+                        // par; Y: slice a is B rows a Q .. a Q + Q - 1
+                        const int off =
+                            isx ? (a >> 1) * S::kPairA + par * S::kLboA +
+                                      ((64 * (a & 1) + cc) >> 3) * 128 + (cc & 7) * 16
+                                : S::kOffB + par * S::kLboB + ((a * Q + cc) >> 3) * 128 +
+                                      (cc & 7) * 16;
+                        *reinterpret_cast<uint4*>(st + off) = v;
                     }
                 }
                 fence_async_smem();
@@ -795,8 +815,9 @@ k_oz_gram(MB<const double> X, MB<const double> Y, int64_t n, double* __restrict_
                     tc_fence_after();
                     const uint32_t st = sbase + slot * S::kStageBytes;
 #pragma unroll
-                    for (int a = 1; a <= kSlices; ++a) {
-                        const uint64_t ad = smem_desc(st + (a - 1) * S::kSliceA, S::kLboA, 128);
+                    for (int j = 0; j < kPairs; ++j) {
+                        const int a = 2 * j + 1;                  // 1-based upper slice
+                        const uint64_t ad = smem_desc(st + j * S::kPairA, S::kLboA, 128);
                         const int na = (kGroups + 1 - a) * Q;
 #pragma unroll
                         for (int n0 = 0; n0 < na; n0 += kMaxN) {
@@ -804,7 +825,7 @@ k_oz_gram(MB<const double> X, MB<const double> Y, int64_t n, double* __restrict_
                             const uint64_t bd =
                                 smem_desc(st + S::kOffB + (n0 / 8) * 128, S::kLboB, 128);
                             mma_bf16(dacc + (uint32_t)((a - 1) * Q + n0), ad, bd,
-                                     idesc_bf16_f32(S::kM, nn), (ks > 0 || a > 1) ? 1u : 0u);
+                                     idesc_bf16_f32(S::kM, nn), (ks > 0 || j > 0) ? 1u : 0u);
                         }
                     }
                     mma_commit(&empty[slot]);
@@ -818,51 +839,82 @@ k_oz_gram(MB<const double> X, MB<const double> Y, int64_t n, double* __restrict_
         }
         __syncwarp();
     } else if (warp >= kGramEpiWarp0) {
-        // ---- epilogue: outputs p = 16 qd + lane (lane < 16), all Q columns
+        // ---- epilogue: row p = 32 (qd & 1) + lane; upper groups (qd < 2) or lower (qd >= 2)
         const int qd = warp & 3;
-        const int p = qd * 16 + (lane & 15);
-        const bool own = lane < 16 && p < P;
-        double acc[Q];
+        const bool upper = qd < 2;
+        const int p = (qd & 1) * 32 + lane;
+        const bool own = p < P;
+        // this thread converts columns c0 .. c0 + QH - 1 and sends the other half
+        const int c0 = upper ? 0 : QH;
+        long long* xsend = reinterpret_cast<long long*>(sm + S::kOffXch + (upper ? 0 : S::kXch));
+        const long long* xrecv =
+            reinterpret_cast<const long long*>(sm + S::kOffXch + (upper ? S::kXch : 0));
+        double acc[QH];
 #pragma unroll
-        for (int q = 0; q < Q; ++q) acc[q] = 0.0;
+        for (int q = 0; q < QH; ++q) acc[q] = 0.0;
         int lt = 0;
         for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++lt) {
             const int buf = lt & 1, set = lt % S::kSets;
-            if (!wait_or_abort(&acc_full[set], (lt / S::kSets) & 1, &abort_flag)) break;
-            if (!wait_or_abort(&cexp_full[buf], (lt >> 1) & 1, &abort_flag)) break;
+            bool ok = wait_or_abort(&acc_full[set], (lt / S::kSets) & 1, &abort_flag);
+            ok = ok && wait_or_abort(&cexp_full[buf], (lt >> 1) & 1, &abort_flag);
+            // the four epilogue warps share named barrier 2: they leave together
+            if (bar_or(2, 128, !ok || abort_flag)) break;
             tc_fence_after();
             const int ep = own ? cexp[buf][p] : 0;
-            int fq[Q];
+            int fq[QH];
 #pragma unroll
-            for (int q = 0; q < Q; ++q) fq[q] = cexp[buf][P + q];
+            for (int q = 0; q < QH; ++q) fq[q] = cexp[buf][P + c0 + q];
             __syncwarp();
             if (lane == 0) mbar_arrive(&cexp_empty[buf]);
             const uint32_t taddr = tbase + ((uint32_t)(qd * 32) << 16) + (uint32_t)set * S::kAcc;
+            long long V[Q];
 #pragma unroll
             for (int col0 = 0; col0 < Q; col0 += 4) {
                 float g[kGroups][4];
+                if (upper) {
 #pragma unroll
-                for (int gi = 0; gi < kGroups; ++gi)
-                    tmem_ld4(taddr + (uint32_t)(gi * Q + col0), g[gi]);
+                    for (int j = 0; j < kGroups; ++j)
+                        tmem_ld4(taddr + (uint32_t)(j * Q + col0), g[j]);
+                } else {
+                    // block j holds group j + 3: group index j + 1; group 2 is upper only
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) g[0][u] = 0.f;
+#pragma unroll
+                    for (int j = 0; j + 1 < kGroups; ++j)
+                        tmem_ld4(taddr + (uint32_t)(j * Q + col0), g[j + 1]);
+                }
                 tmem_wait_ld();
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
                     float gu[kGroups];
 #pragma unroll
                     for (int gi = 0; gi < kGroups; ++gi) gu[gi] = g[gi][u];
-                    const long long v = combine_groups(gu);
-                    acc[col0 + u] =
-                        fma((double)v, pow2_biased(ep + fq[col0 + u] - 1077), acc[col0 + u]);
+                    V[col0 + u] = combine_groups(gu);
                 }
             }
+            // the accumulator is read: the MMA warp may start the next tile in it
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&acc_empty[set]);
+            // (register arrays indexed with constants only: the halves are selected per lane)
+            long long mine[QH];
+#pragma unroll
+            for (int q = 0; q < QH; ++q) {
+                xsend[p * QH + q] = upper ? V[QH + q] : V[q];
+                mine[q] = upper ? V[q] : V[QH + q];
+            }
+            asm volatile("bar.sync 2, 128;" ::: "memory");
+#pragma unroll
+            for (int q = 0; q < QH; ++q) {
+                const long long v = mine[q] + xrecv[p * QH + q];
+                acc[q] = fma((double)v, pow2_biased(ep + fq[q] - 1077), acc[q]);
+            }
+            asm volatile("bar.sync 2, 128;" ::: "memory");   // exchange buffers reusable
         }
         if (own) {
-            double* out = partials + (int64_t)blockIdx.x * 4096 + p * Q;
+            double* out = partials + (int64_t)blockIdx.x * 4096 + p * Q + c0;
 #pragma unroll
-            for (int q = 0; q < Q; ++q) out[q] = acc[q];
+            for (int q = 0; q < QH; ++q) out[q] = acc[q];
         }
     }
     __syncthreads();
