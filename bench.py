@@ -61,13 +61,19 @@ def parse():
     ap.add_argument("--precond", default=None, choices=["ic0"],
                     help="block Jacobi split preconditioning, IC(0) blocks on 64 boxes")
     ap.add_argument("--sweep", action="store_true",
-                    help="stability sweep over s in {1,2,4,8} and both precisions")
+                    help="stability sweep over bases, s in {1,2,4,8} and both precisions")
+    ap.add_argument("--sweep-bases", default="sstep,ca5,ca7,restructured",
+                    help="comma-separated Krylov bases for --sweep")
     ap.add_argument("--tol", type=float, default=1e-8)
     ap.add_argument("--maxit", type=int, default=20000)
-    ap.add_argument("--cpu-sample-iters", type=int, default=2)
+    ap.add_argument("--cpu-sample-iters", type=int, default=4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--host-loop", action="store_true",
+                    help="test convergence on the host every iteration instead of inside the "
+                         "CUDA graph of conditional iterations (same kernels; for profilers "
+                         "that take one kernel launch at a time)")
     return ap.parse_args()
 
 
@@ -317,10 +323,14 @@ def run_batched(args, rank, world, dist):
 
 
 def run_sweep(args, rank):
-    """Stability sweep: s in {1, 2, 4, 8} x {float64, FP32_IR} on one workload (s-step SRE-CG,
-    Algorithm 4), one timed solve each after a short warm-up.  Per entry: s-step iterations,
-    status, time, true relative residual and the relative difference of x from the float64
-    s = 1 solution; per precision, the largest s that reached the tolerance."""
+    """Stability sweep of s-step SRE-CG (Algorithm 4) over the Krylov basis (s-step monomial
+    basis of Algorithm 4, the CA forms of Algorithms 5 and 7, the restructured basis of
+    Algorithm 1), s in {1, 2, 4, 8} and both precisions, one timed solve each after a short
+    warm-up.  The first row of each basis and precision fixes the iteration budget of the
+    others at four times its s-step iterations (scaled by 1/s), so an unstable configuration
+    ends quickly at EKCG_MAXIT or breakdown.  Per entry: s-step iterations, status, time,
+    true relative residual and the relative difference of x from the float64 s = 1 solution;
+    per basis and precision, the largest s that reached the tolerance."""
     import torch
     from paper_1804_10629_gb300 import ekcg
     cfg = WORKLOADS[args.workload]
@@ -329,32 +339,50 @@ def run_sweep(args, rank):
     Asp = prob.A.to_scipy()
     nb = float(np.linalg.norm(prob.b))
     rows, ref = [], None
-    for prec in ("fp64", "fp32_ir"):
-        for s in (1, 2, 4, 8):
-            S = ekcg.Solver(prob.A, prob.t, prob.part, variant="sre", precision=prec, max_s=s)
-            x = torch.empty_like(b)
-            S.solve(b, s=s, tol=args.tol, maxit=20, x=x)
-            torch.cuda.synchronize()
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record()
-            x, its, hist, st = S.solve(b, s=s, tol=args.tol, maxit=args.maxit, x=x)
-            e1.record()
-            torch.cuda.synchronize()
-            xs = x.cpu().numpy()
-            if ref is None:
-                ref = xs.copy()
-            rows.append({"precision": prec, "s": s, "iters": int(its), "status": int(st),
-                         "seconds": e0.elapsed_time(e1) / 1e3,
-                         "true_relres": float(np.linalg.norm(prob.b - Asp @ xs) / nb),
-                         "x_rel_diff_vs_fp64_s1": float(np.linalg.norm(xs - ref) /
-                                                        np.linalg.norm(ref))})
-            S.close()
+    bases = [v for v in args.sweep_bases.split(",") if v]
+    for basis in bases:
+        for prec in ("fp64", "fp32_ir"):
+            budget = None
+            for s in (1, 2, 4, 8):
+                maxit = args.maxit if budget is None else max(8, (4 * budget) // s)
+                try:
+                    S = ekcg.Solver(prob.A, prob.t, prob.part, variant="sre", basis=basis,
+                                    precision=prec, max_s=s)
+                except ekcg.EkcgError as e:
+                    rows.append({"basis": basis, "precision": prec, "s": s,
+                                 "error": str(e)})
+                    continue
+                x = torch.empty_like(b)
+                S.solve(b, s=s, tol=args.tol, maxit=min(20, maxit), x=x)
+                torch.cuda.synchronize()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record()
+                x, its, hist, st = S.solve(b, s=s, tol=args.tol, maxit=maxit, x=x)
+                e1.record()
+                torch.cuda.synchronize()
+                xs = x.cpu().numpy()
+                S.close()
+                ok = bool(np.all(np.isfinite(xs)))
+                if ref is None and ok:
+                    ref = xs.copy()
+                if budget is None:
+                    budget = int(its) * s
+                rows.append({"basis": basis, "precision": prec, "s": s, "iters": int(its),
+                             "maxit": maxit, "status": int(st),
+                             "seconds": e0.elapsed_time(e1) / 1e3,
+                             "true_relres": float(np.linalg.norm(prob.b - Asp @ xs) / nb)
+                             if ok else None,
+                             "x_rel_diff_vs_fp64_s1": float(np.linalg.norm(xs - ref) /
+                                                            np.linalg.norm(ref))
+                             if ok and ref is not None else None})
     largest = {}
-    for prec in ("fp64", "fp32_ir"):
-        ok = [r["s"] for r in rows if r["precision"] == prec and r["status"] == 0
-              and r["true_relres"] <= args.tol * 1.01]
-        largest[prec] = max(ok) if ok else None
+    for basis in bases:
+        for prec in ("fp64", "fp32_ir"):
+            good = [r["s"] for r in rows if r["basis"] == basis and r["precision"] == prec
+                    and r.get("status") == 0 and r.get("true_relres") is not None
+                    and r["true_relres"] <= args.tol * 1.01]
+            largest[f"{basis}/{prec}"] = max(good) if good else None
     if rank == 0:
         print(json.dumps({"sweep": prob.name, "n": prob.A.n, "t": prob.t, "tol": args.tol,
                           "rows": rows, "largest_stable_s": largest}), flush=True)
@@ -434,21 +462,26 @@ def oracle_counts():
 
 
 def cpu_oracle_sample(prob, s, variant, iters, gpu_iters=None, full_size=True):
-    """Time `iters` s-step iterations of the FP64 oracle on the full problem; scale to a
-    whole solve by the oracle's stored iteration count (full-size workloads only), else by
-    the GPU's."""
+    """Whole-solve time of the FP64 oracle from a bounded sample: one call with no
+    iteration (setup, permutation, initial residual) and one with `iters` s-step
+    iterations; the difference gives the time per iteration, and the estimate is the setup
+    time plus that per-iteration time times the oracle's stored iteration count
+    (full-size workloads), else the GPU's."""
     from oracle import ekcg_ref as o
+    t0 = time.perf_counter()
+    o.solve(prob.A, prob.b, prob.part, prob.t, s, tol=1e-8, maxit=0, variant=variant)
+    t_setup = time.perf_counter() - t0
     t0 = time.perf_counter()
     res = o.solve(prob.A, prob.b, prob.part, prob.t, s, tol=1e-8, maxit=iters, variant=variant)
     dt = time.perf_counter() - t0
-    per_it = dt / max(res.iters, 1)
+    per_it = max(dt - t_setup, 0.0) / max(res.iters, 1)
     key = f"{prob.name.split('-')[0].lower()}/t{prob.t}/s{s}/{variant}/sstep/fp64"
     cnt = oracle_counts().get(key, {}).get("iters") if full_size else None
     scale_src = "oracle_counts.json" if cnt else "GPU iteration count"
     total = cnt if cnt else (gpu_iters or res.iters)
-    return {"value": per_it * total, "per_iter_s": per_it, "iters_scaled_to": total,
-            "scaled_by": scale_src, "sample_s": dt, "sample_iters": res.iters,
-            "cores": len(os.sched_getaffinity(0))}
+    return {"value": t_setup + per_it * total, "per_iter_s": per_it, "setup_s": t_setup,
+            "iters_scaled_to": total, "scaled_by": scale_src, "sample_s": dt + t_setup,
+            "sample_iters": res.iters, "cores": len(os.sched_getaffinity(0))}
 
 
 def run_reference(args, rank, world):
@@ -475,8 +508,9 @@ def run_reference(args, rank, world):
         "config": {"workload": f"{prob.name} n={prob.A.n} nnz={prob.A.nnz} t={prob.t} s={s} "
                                f"{variant} sstep fp64", "parallelism": "replicas"},
         "cpu_baseline": {"value": v, "unit": "s", "cores": samples[0]["cores"], "kind": "oracle",
-                         "sample": f"{args.cpu_sample_iters} s-step iterations of the FP64 oracle "
-                                   f"per step on the full workload, scaled to "
+                         "sample": f"setup plus {args.cpu_sample_iters} s-step iterations of the "
+                                   f"FP64 oracle per step on the full workload; setup time plus "
+                                   f"the per-iteration time x "
                                    f"{samples[0]['iters_scaled_to']} iterations "
                                    f"({samples[0]['scaled_by']})"},
         "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -520,6 +554,8 @@ def main():
                         precision=args.precision, max_s=s, profile=True,
                         stream=stream.cuda_stream, max_basis_bytes=64 << 30,
                         contraction=args.contraction)
+    if args.host_loop:
+        S.set_device_loop(False)   # the convergence test on the host, every iteration
     if args.precond:
         # block Jacobi over 64 geometric boxes (the paper's 64 subdomains), each inside one
         # of the workload's t domains
@@ -583,9 +619,10 @@ def main():
         r = cpu_oracle_sample(prob, s, variant, args.cpu_sample_iters, gpu_iters=its,
                               full_size=not args.grid)
         cpu = {"value": r["value"], "unit": "s", "cores": r["cores"], "kind": "oracle",
-               "sample": f"{r['sample_iters']} s-step iterations of the FP64 oracle on the full "
-                         f"workload ({r['sample_s']:.1f} s), scaled to {r['iters_scaled_to']} "
-                         f"iterations ({r['scaled_by']})"}
+               "sample": f"setup ({r['setup_s']:.1f} s) and {r['sample_iters']} s-step "
+                         f"iterations of the FP64 oracle on the full workload "
+                         f"({r['sample_s']:.1f} s in all); setup plus the per-iteration time "
+                         f"x {r['iters_scaled_to']} iterations ({r['scaled_by']})"}
 
     if rank == 0:
         line = {
@@ -603,6 +640,9 @@ def main():
                        "true_relres": relres, "status": st,
                        "l2": "working set larger than L2 (matrix + n x t blocks)",
                        "setup_s": setup_s, "parallelism": "replicas",
+                       "convergence_test": ("host, every iteration" if args.host_loop else
+                                            "device, inside a CUDA graph of conditional "
+                                            "iterations"),
                        "precond": ("block Jacobi, IC(0) blocks on 64 boxes" if args.precond
                                    else None),
                        "profiling": "timed solves without per-launch events; kernel table from one more solve with CUDA events around every launch"},

@@ -266,9 +266,8 @@ int ekcg_gram_with(ekcg_ctx* ctx, const double* X, int p, const double* Y, int q
  * doubles), present on every GPU that loads the library until the process exits; no call
  * allocates or frees memory.  The first call on a device looks up the array's device
  * address (cudaGetSymbolAddress) with that device current; make that first call before any
- * stream capture.  The looked-up address is kept per device ordinal for the life of the
- * process: it does not survive a device reset (cudaDeviceReset, or a reset of the primary
- * context), after which calls on that device must not be made.  Every call shares the array and each call overwrites every entry it later
+ * stream capture.  The address is kept per device for the life of the process and does not
+ * survive a device reset: make no call on a device after cudaDeviceReset.  Every call shares the array and each call overwrites every entry it later
  * reads, so nothing has to be cleared between calls; calls that overlap on the GPU (other
  * streams, other host threads) race on the array and must be serialised by the caller.
  * Errors: EKCG_EINVAL (sizes, null pointers), EKCG_ECUDA (lookup or launch failure).     */

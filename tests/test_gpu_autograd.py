@@ -101,7 +101,9 @@ def test_differentiable_workload_full_size_against_oracle_record():
     target x* (field seed 5, b = 1), the forward solve x (field seed 4, b = 1), the adjoint
     solve A lambda = x - x* and dL/dlog kappa, each against the oracle's whole-solve record
     (tests/golden/oracle_counts.json, written by the oracle only): iteration counts within
-    one, the first 21 residual norms to 1e-6, the true relative residual, and x, lambda
+    the spread of oracle solves whose right-hand side was perturbed at the rounding level
+    (the counts are chaotic in rounding at this size), widened by one; the first 21
+    residual norms to 1e-6, the true relative residual, and x, lambda
     and the gradient at 256 sampled rows (float64 tolerances relative to the max-norm of
     the oracle's vector: 1e-8 for x*, x and lambda, 1e-7 for the gradient, a product of
     two solutions)."""
@@ -119,12 +121,19 @@ def test_differentiable_workload_full_size_against_oracle_record():
     val = torch.empty(A.nnz, dtype=torch.float64, device="cuda")
     one = torch.ones(N * N, dtype=torch.float64, device="cuda")
 
-    def solve(log_k, rhs, rec, Amat, rhs_np):
+    def spread(which):
+        pre = f"{key}/{which}/perturbed/"
+        return [gold[f"{key}/{which}"]["iters"]] + [v["iters"] for k, v in gold.items()
+                                                    if k.startswith(pre)]
+
+    def solve(log_k, rhs, which, Amat, rhs_np):
+        rec = gold[f"{key}/{which}"]
         ekcg.ekcg_diffusion2d_values(S.ctx, N, N, 1.0, 1.0,
                                      torch.as_tensor(log_k.ravel(), device="cuda"), val)
         ekcg.ekcg_update_values(S.ctx, val)
         x, it, hist, st = S.solve(rhs, s=s, tol=1e-8, maxit=5000)
-        assert st == 0 and abs(it - rec["iters"]) <= 1, (it, rec["iters"])
+        counts = spread(which)
+        assert st == 0 and min(counts) - 1 <= it <= max(counts) + 1, (it, counts)
         np.testing.assert_allclose(hist[:21], rec["hist"][:21], rtol=1e-6)
         xh = x.cpu().numpy()
         assert (np.linalg.norm(rhs_np - Amat.to_scipy() @ xh) <= 1.01e-8 *
@@ -134,10 +143,10 @@ def test_differentiable_workload_full_size_against_oracle_record():
         assert np.max(np.abs(xh[rows] - ref)) <= 1e-8 * rec["x"]["norminf"]
         return x, xh
 
-    xs, xsh = solve(lk_star, one, gold[key + "/target"], A_star, np.ones(N * N))
-    x, xh = solve(lk, one, gold[key + "/forward"], A, np.ones(N * N))
+    xs, xsh = solve(lk_star, one, "target", A_star, np.ones(N * N))
+    x, xh = solve(lk, one, "forward", A, np.ones(N * N))
     g = x - xs
-    lam, lamh = solve(lk, g.contiguous(), gold[key + "/adjoint"], A, g.cpu().numpy())
+    lam, lamh = solve(lk, g.contiguous(), "adjoint", A, g.cpu().numpy())
     glk = torch.empty(N * N, dtype=torch.float64, device="cuda")
     ekcg.ekcg_diffusion2d_grad_logkappa(S.ctx, N, N, 1.0, 1.0,
                                         torch.as_tensor(lk.ravel(), device="cuda"), lam, x, glk)
