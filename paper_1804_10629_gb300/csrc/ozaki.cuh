@@ -188,6 +188,13 @@ __device__ __forceinline__ uint32_t pack_bf16(uint32_t f0, uint32_t f1) {
     return __byte_perm(f0, f1, 0x7632);
 }
 
+// 16-byte global -> shared copy by this thread (cp.async); src_bytes 0 writes zeros
+__device__ __forceinline__ void cp_async16_zfill(void* dst, const void* src, uint32_t src_bytes) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(bulk::smem_addr(dst)),
+                 "l"(src), "r"(src_bytes)
+                 : "memory");
+}
+
 // ---- the update -------------------------------------------------------------------------
 // One persistent CTA per SM, warp-specialised:
 //   warps 0-7  (slicers): per 128-row tile, load the tile's X values (each thread half a row,
@@ -214,7 +221,7 @@ constexpr int kPrefetchWarp = 13;
 constexpr int kUpdThreads = 14 * 32;
 constexpr int kPrefetchAhead = 2;   // tiles of lead of the L2 prefetch
 constexpr int kKS = 16;          // columns of X per ring stage (one MMA K-step)
-constexpr int kStages = 4;
+constexpr int kStages = 3;
 
 template <int P, int Q>
 struct UpdShape {
@@ -226,7 +233,12 @@ struct UpdShape {
     // the nine C slices are stacked along N (B row (b - 1) Q + q), so one MMA of N =
     // (10 - a) Q per X slice a deposits every pair (a, b) into group a + b
     static constexpr int kOffB = kStages * kStageBytes;
-    static constexpr int kSmem = kOffB + kSlices * kSliceB + 1024;  // + alignment slack
+    // the next tile's X values, copied by the slicers themselves (cp.async), in chunks of
+    // 16 bytes laid out [chunk][slicer thread] so that every access is conflict-free
+    static constexpr int kOffRaw = kOffB + kSlices * kSliceB;
+    static constexpr int kRawChunks = P / 4;                       // per slicer thread
+    static constexpr int kSmem = kOffRaw + kRawChunks * kSlicerWarps * 32 * 16 + 1024;
+    static_assert(kSmem <= 232448, "shared memory");
     static constexpr int kLboA = (kTile / 8) * 128;                // next 8 columns of A
     static constexpr int kLboB = (kSlices * Q / 8) * 128;          // next 8 columns of B
     static constexpr uint32_t kAcc = (uint32_t)(kGroups * Q);      // columns of one set
@@ -371,6 +383,24 @@ k_oz_update(MB<const double> X, const double* __restrict__ C, MB<const double> Y
     if (warp < kSlicerWarps) {
         // ---- slicers: thread = (row r, half h); the half holds column groups h + 2j
         const int r = warp * 16 + (lane & 15), h = lane >> 4;
+        // this thread's row of a tile, copied one tile ahead into its own 16-byte chunks
+        unsigned char* xbuf = sm + S::kOffRaw + tid * 16;
+        auto copy_ahead = [&](int64_t tl) {
+            if (tl < ntiles) {
+                const int64_t i = tl * kTile + r;
+#pragma unroll
+                for (int j = 0; j < P / 16; ++j) {
+                    const int col = (h + 2 * j) * 8, b = col / X.w;
+                    const double* src = X.blk(b) + (i < n ? i : 0) * X.w + (col - b * X.w);
+#pragma unroll
+                    for (int u = 0; u < 4; ++u)
+                        cp_async16_zfill(xbuf + (j * 4 + u) * (kSlicerWarps * 32 * 16),
+                                         src + 2 * u, i < n ? 16u : 0u);
+                }
+            }
+            asm volatile("cp.async.commit_group;" ::: "memory");
+        };
+        copy_ahead(blockIdx.x);
         int stage = 0;
         int lt = 0;
         for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++lt) {
@@ -378,20 +408,18 @@ k_oz_update(MB<const double> X, const double* __restrict__ C, MB<const double> Y
             if (lt >= 2 && !wait_or_abort(&erow_empty[buf], ((lt >> 1) - 1) & 1, &abort_flag))
                 break;
             if (tid == 0) started = lt + 1;
-            const int64_t i = tile * kTile + r;
             double xv[P / 2];
+            asm volatile("cp.async.wait_group 0;" ::: "memory");
 #pragma unroll
-            for (int j = 0; j < P / 16; ++j) {
-                const int col = (h + 2 * j) * 8, b = col / X.w;
-                const double2* src =
-                    reinterpret_cast<const double2*>(X.blk(b) + i * X.w + (col - b * X.w));
+            for (int j = 0; j < P / 16; ++j)
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
-                    const double2 v = (i < n) ? src[u] : make_double2(0.0, 0.0);
+                    const double2 v = *reinterpret_cast<const double2*>(
+                        xbuf + (j * 4 + u) * (kSlicerWarps * 32 * 16));
                     xv[j * 8 + 2 * u] = v.x;
                     xv[j * 8 + 2 * u + 1] = v.y;
                 }
-            }
+            copy_ahead(tile + gridDim.x);   // lands while this tile is cut
             int e = 0;
 #pragma unroll
             for (int u = 0; u < P / 2; ++u) e = max(e, bexp(xv[u]));
@@ -441,6 +469,7 @@ k_oz_update(MB<const double> X, const double* __restrict__ C, MB<const double> Y
             }
             if (!ok) break;
         }
+        asm volatile("cp.async.wait_group 0;" ::: "memory");   // no copy outlives the CTA
     } else if (warp == kMmaWarp) {
         // ---- MMA issue (one thread)
         if (lane == 0) {
@@ -501,39 +530,47 @@ k_oz_update(MB<const double> X, const double* __restrict__ C, MB<const double> Y
         // ---- epilogue: quarter qd = warp % 4, rows 32 qd + lane of the tile
         const int qd = warp & 3;
         const int m = qd * 32 + lane;
+        // Y values of 8 columns of this thread's row (zero past n or without Y)
+        auto load_y = [&](int64_t ri, int col0, double (&yv)[8]) {
+            if (beta_on && ri < n) {
+                const double2* yr = reinterpret_cast<const double2*>(Y.blk(0) + ri * Y.w + col0);
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const double2 v = yr[u];
+                    yv[2 * u] = v.x;
+                    yv[2 * u + 1] = v.y;
+                }
+            } else {
+#pragma unroll
+                for (int u = 0; u < 8; ++u) yv[u] = 0.0;
+            }
+        };
         int lt = 0;
         for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++lt) {
             const int buf = lt & 1, set = lt % S::kSets;
+            const int64_t ri = tile * kTile + m;
+            // the first Y columns are requested before the accumulator is ready
+            double ynext[8];
+            load_y(ri, 0, ynext);
             if (!wait_or_abort(&acc_full[set], (lt / S::kSets) & 1, &abort_flag)) break;
             if (!wait_or_abort(&erow_full[buf], (lt >> 1) & 1, &abort_flag)) break;
             tc_fence_after();
-            const int64_t ri = tile * kTile + m;
             const int er = erow[buf][m];
             __syncwarp();
             if (lane == 0) mbar_arrive(&erow_empty[buf]);
             const uint32_t taddr = tbase + ((uint32_t)(qd * 32) << 16) + (uint32_t)set * S::kAcc;
 #pragma unroll 1
             for (int col0 = 0; col0 < Q; col0 += 8) {
+                double yv[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) yv[u] = ynext[u];
+                if (col0 + 8 < Q) load_y(ri, col0 + 8, ynext);   // one chunk ahead
                 float g[kGroups][8];
 #pragma unroll
                 for (int gi = 0; gi < kGroups; ++gi)
                     tmem_ld8(taddr + (uint32_t)(gi * Q + col0), g[gi]);
                 tmem_wait_ld();
                 if (ri < n) {
-                    double yv[8];
-                    if (beta_on) {
-                        const double2* yr =
-                            reinterpret_cast<const double2*>(Y.blk(0) + ri * Y.w + col0);
-#pragma unroll
-                        for (int u = 0; u < 4; ++u) {
-                            const double2 v = yr[u];
-                            yv[2 * u] = v.x;
-                            yv[2 * u + 1] = v.y;
-                        }
-                    } else {
-#pragma unroll
-                        for (int u = 0; u < 8; ++u) yv[u] = 0.0;
-                    }
                     double ov[8];
 #pragma unroll
                     for (int u = 0; u < 8; ++u) {
@@ -581,26 +618,30 @@ k_oz_update(MB<const double> X, const double* __restrict__ C, MB<const double> Y
 // fp32 sum stays exact (5 x 64 rows x 127^2 < 2^24).  Five MMAs per K-step (slice 10 is
 // zero) instead of nine at M = 64.
 //
-//   warp 7     (producer): one thread copies the tile's rows of every X block and of Y
+//   warps 0-7  (slicers): warp w cuts row group w of the tile (rows 8 w .. 8 w + 7), lane =
+//              column within each 32-column block of X | Y; pass 1 takes the column
+//              binades of the tile (per-warp maxima in shared memory, then the max over the
+//              eight row groups), pass 2 writes the warp's 8 rows of every slice into the
+//              stage of its K-step (w / 2), K-group w % 2.  Two slicer warps per SM
+//              sub-partition;
+//   warp 8     (MMA): per K-step the five pair MMAs (M = 128, K = 16, N in pieces <= 256);
+//   warp 9     (producer): one thread copies the tile's rows of every X block and of Y
 //              (contiguous runs of 64 x w doubles) into one of two raw shared buffers with
 //              bulk copies completing on an mbarrier, one tile ahead of the slicers;
-//   warps 0 .. 2 nb - 1 (slicers, nb = ceil((P + Q) / 32) column blocks): lane = column,
-//              warp = (column block, row parity); pass 1 takes the column binades of the
-//              tile from the raw buffer (a shared max over the two row parities), pass 2
-//              cuts 8 rows x 1 column per thread and K-step into the stage ring;
-//   warp 6     (MMA): per K-step the five pair MMAs (M = 128, K = 16, N in pieces <= 256);
-//   warps 8-11 (epilogue): warp 8 + q reads lane quarter q, so the thread for output row
-//              p = 32 (q & 1) + lane holds the upper groups (q < 2) or the lower groups
-//              (q >= 2) of that row.  Each combines its groups into a 64-bit integer per
-//              column, releases the accumulator to the MMA warp, and exchanges half of the
-//              columns through shared memory with its partner (same row, other half), so
-//              that each thread converts and scales Q / 2 of the row's outputs.
-constexpr int kGramThreads = 12 * 32;
-constexpr int kGramMmaWarp = 6;
-constexpr int kGramProducerWarp = 7;
-constexpr int kGramEpiWarp0 = 8;
+//   warps 10-13 (epilogue): warp w reads lane quarter q = w % 4 of the accumulator; the
+//              thread for output row p = 32 (q & 1) + lane holds the upper groups (q < 2,
+//              lanes 0-63) or the lower groups (q >= 2, lanes 64-127) of that row.  It
+//              combines the half of the columns its partner (same row, other half)
+//              converts and leaves it in shared memory, combines its own half, releases the
+//              accumulator to the MMA warp, adds the partner's values and converts and
+//              scales Q / 2 outputs.
+constexpr int kGramSlicers = 8;
+constexpr int kGramMmaWarp = 8;
+constexpr int kGramProducerWarp = 9;
+constexpr int kGramEpiWarp0 = 10;
+constexpr int kGramThreads = 14 * 32;
 constexpr int kGramRows = 64;        // rows per tile (binade scope, exact fp32 sums)
-constexpr int kGramStages = 3;
+constexpr int kGramStages = 4;      // one tile of K-steps: no stage is reused within a tile
 constexpr int kPairs = (kSlices + 1) / 2;   // X slice pairs per K-step (the last one half zero)
 
 template <int P, int Q>
@@ -615,7 +656,7 @@ struct GramShape {
     static constexpr int kRawX = kGramRows * P * 8;                // raw X tile, bytes
     static constexpr int kRawY = kGramRows * Q * 8;
     static constexpr int kOffRaw = kGramStages * kStageBytes;      // raw buffers after ring
-    static constexpr int kXch = 64 * (Q / 2) * 8;                  // one exchange direction
+    static constexpr int kXch = 64 * 8 * 8;                        // one direction, 8 columns
     static constexpr int kOffXch = kOffRaw + 2 * (kRawX + kRawY);
     static constexpr int kSmem = kOffXch + 2 * kXch + 1024;
     static constexpr int kLboA = (kM / 8) * 128;                   // 2 KB
@@ -625,8 +666,8 @@ struct GramShape {
     static constexpr uint32_t kCols = 512;
     static constexpr int kT = P + Q;                               // columns sliced per row
     static constexpr int kNB = (kT + 31) / 32;                     // column blocks
-    static constexpr int kSlicers = 2 * kNB;                       // slicer warps (<= 6)
     static constexpr int kKSteps = kGramRows / kKS;                // 4
+    static_assert(kKSteps * 2 == kGramSlicers, "one slicer warp per 8-row group");
     static_assert(kSmem <= 232448, "shared memory");
 };
 
@@ -643,8 +684,8 @@ k_oz_gram(MB<const double> X, MB<const double> Y, int64_t n, double* __restrict_
     __shared__ __align__(8) uint64_t acc_full[2], acc_empty[2], cexp_full[2], cexp_empty[2], fin;
     __shared__ __align__(8) uint64_t raw_full[2], raw_empty[2];
     __shared__ uint32_t tslot;
-    __shared__ int cexp[2][S::kT];          // tile binades: X columns, then Y columns
-    __shared__ int cmax[2][S::kNB * 32];    // per row parity, pass 1
+    __shared__ int cexp[2][S::kT];                    // tile binades: X columns, then Y
+    __shared__ int cmax[kGramSlicers][S::kNB * 32];   // per row group, pass 1
     __shared__ volatile int abort_flag;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t sbase = bulk::smem_addr(sm);
@@ -656,16 +697,16 @@ k_oz_gram(MB<const double> X, MB<const double> Y, int64_t n, double* __restrict_
     if (warp == 0) tmem_alloc(&tslot, S::kCols);
     if (tid == 0) {
         for (int i = 0; i < kGramStages; ++i) {
-            bulk::mbar_init(&full[i], S::kSlicers);
+            bulk::mbar_init(&full[i], 2);            // the two row groups of a K-step
             bulk::mbar_init(&empty[i], 1);
         }
         for (int b = 0; b < 2; ++b) {
             bulk::mbar_init(&acc_full[b], 1);
             bulk::mbar_init(&acc_empty[b], 4);
-            bulk::mbar_init(&cexp_full[b], S::kSlicers);
+            bulk::mbar_init(&cexp_full[b], kGramSlicers);
             bulk::mbar_init(&cexp_empty[b], 4);
             bulk::mbar_init(&raw_full[b], 1);
-            bulk::mbar_init(&raw_empty[b], S::kSlicers);
+            bulk::mbar_init(&raw_empty[b], kGramSlicers);
         }
         bulk::mbar_init(&fin, 1);
         abort_flag = 0;
@@ -681,19 +722,24 @@ k_oz_gram(MB<const double> X, MB<const double> Y, int64_t n, double* __restrict_
     const uint32_t tbase = tslot;
     const int64_t ntiles = (n + kGramRows - 1) / kGramRows;
 
-    if (warp < S::kSlicers) {
-        // ---- slicers: column c = 32 (warp / 2) + lane (X columns first), row parity warp % 2
-        const int cb = warp >> 1, par = warp & 1;
-        const int c = cb * 32 + lane;
-        const bool active = c < S::kT;
-        const bool isx = c < P;
-        const int cc = isx ? c : c - P;                   // column inside X or Y
-        const int w = isx ? X.w : Q;
-        const int blk = (active && isx) ? cc / X.w : 0;
-        const int cw = active ? cc - blk * w : 0;
-        // raw element (row, column) = raw[blk * 64 * w + row * w + cw]
-        const int raw_off = blk * kGramRows * w + cw;
-        int stage = 0;
+    if (warp < kGramSlicers) {
+        // ---- slicers: rows 8 rg .. 8 rg + 7 of the tile; column 32 cb + lane of X | Y
+        const int rg = warp, ks = rg >> 1, par = rg & 1;
+        int raw_off[S::kNB], wcol[S::kNB];
+        bool act[S::kNB], isxc[S::kNB];
+#pragma unroll
+        for (int cb = 0; cb < S::kNB; ++cb) {
+            const int c = cb * 32 + lane;
+            act[cb] = c < S::kT;
+            isxc[cb] = c < P;
+            const int cc = isxc[cb] ? c : c - P;
+            const int w = isxc[cb] ? X.w : Q;
+            const int blk = (act[cb] && isxc[cb]) ? cc / X.w : 0;
+            const int cw = act[cb] ? cc - blk * w : 0;
+            // raw element (row, column) = raw[blk * 64 * w + row * w + cw]
+            raw_off[cb] = blk * kGramRows * w + cw + 8 * rg * w;
+            wcol[cb] = w;
+        }
         int lt = 0;
         bool failed = false;   // the slicer warps leave together (they share named barriers)
         for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++lt) {
@@ -703,49 +749,58 @@ k_oz_gram(MB<const double> X, MB<const double> Y, int64_t n, double* __restrict_
                 failed = true;
             if (!failed && !wait_or_abort(&raw_full[buf], (lt >> 1) & 1, &abort_flag))
                 failed = true;
-            if (bar_or(1, S::kSlicers * 32, failed || abort_flag)) break;
+            if (bar_or(1, kGramSlicers * 32, failed || abort_flag)) break;
             const int64_t r0 = tile * kGramRows;
             const int rows = (int)((n - r0) < kGramRows ? (n - r0) : kGramRows);
-            const double* raw = (isx ? rawx[buf] : rawy[buf]) + raw_off;
-            // pass 1: binade of the column over the tile (this parity's row groups)
-            int e = 0;
-            if (active) {
+            const int myrows = rows - 8 * rg;            // rows of this group (may be <= 0)
+            // pass 1: binade of each column over this row group, then over the tile
+            int e[S::kNB];
 #pragma unroll
-                for (int rg = par; rg < kGramRows / 8; rg += 2)
+            for (int cb = 0; cb < S::kNB; ++cb) {
+                const double* raw = (isxc[cb] ? rawx[buf] : rawy[buf]) + raw_off[cb];
+                int m = 0;
+                if (act[cb]) {
 #pragma unroll
                     for (int u = 0; u < 8; ++u)
-                        if (rg * 8 + u < rows) e = max(e, bexp(raw[(rg * 8 + u) * w]));
+                        if (u < myrows) m = max(m, bexp(raw[u * wcol[cb]]));
+                }
+                cmax[rg][cb * 32 + lane] = m;
             }
-            cmax[par][cb * 32 + lane] = e;
-            asm volatile("bar.sync 1, %0;" ::"r"(S::kSlicers * 32) : "memory");
-            e = max(cmax[0][cb * 32 + lane], cmax[1][cb * 32 + lane]);
-            if (par == 0 && active) cexp[buf][c] = e;
-            asm volatile("bar.sync 1, %0;" ::"r"(S::kSlicers * 32) : "memory");
+            asm volatile("bar.sync 1, %0;" ::"r"(kGramSlicers * 32) : "memory");
+#pragma unroll
+            for (int cb = 0; cb < S::kNB; ++cb) {
+                int m = 0;
+#pragma unroll
+                for (int r = 0; r < kGramSlicers; ++r) m = max(m, cmax[r][cb * 32 + lane]);
+                e[cb] = m;
+                if (rg == 0 && act[cb]) cexp[buf][cb * 32 + lane] = m;
+            }
+            asm volatile("bar.sync 1, %0;" ::"r"(kGramSlicers * 32) : "memory");
             __syncwarp();
             if (lane == 0) mbar_arrive(&cexp_full[buf]);
-            // pass 2: K-step ks = row groups 2 ks, 2 ks + 1; this warp holds group 2 ks + par
-            for (int ks = 0; ks < S::kKSteps; ++ks) {
-                const int slot = stage % kGramStages, use = stage / kGramStages;
-                ++stage;
-                if (failed) continue;
-                if (use >= 1 && !wait_or_abort(&empty[slot], (use - 1) & 1, &abort_flag)) {
-                    failed = true;
-                    continue;
-                }
-                if (active) {
-                    const int rb = (2 * ks + par) * 8;
+            // pass 2: this row group's 8 rows of every slice, into the stage of K-step ks
+            const int stage = lt * S::kKSteps + ks;
+            const int slot = stage % kGramStages, use = stage / kGramStages;
+            if (use >= 1 && !wait_or_abort(&empty[slot], (use - 1) & 1, &abort_flag))
+                failed = true;
+            if (!failed) {
+                unsigned char* st = sm + slot * S::kStageBytes;
+#pragma unroll
+                for (int cb = 0; cb < S::kNB; ++cb) {
+                    if (!act[cb]) continue;
+                    const double* raw = (isxc[cb] ? rawx[buf] : rawy[buf]) + raw_off[cb];
+                    const int cc = isxc[cb] ? cb * 32 + lane : cb * 32 + lane - P;
                     uint64_t F[8];
                     uint32_t ms[8];
                     float undo[8];
 #pragma unroll
                     for (int u = 0; u < 8; ++u) {
-                        const double x = (rb + u < rows) ? raw[(rb + u) * w] : 0.0;
-                        F[u] = fixed63(x, e);
+                        const double x = (u < myrows) ? raw[u * wcol[cb]] : 0.0;
+                        F[u] = fixed63(x, e[cb]);
                         const bool neg = (__double_as_longlong(x) >> 63) != 0;
                         ms[u] = sign_magic(neg);
                         undo[u] = sign_undo(neg);
                     }
-                    unsigned char* st = sm + slot * S::kStageBytes;
 #pragma unroll
                     for (int a = 0; a < kSlices; ++a) {
                         uint4 v;
@@ -760,10 +815,10 @@ k_oz_gram(MB<const double> X, MB<const double> Y, int64_t n, double* __restrict_
                         // X: slice a (0-based) in pair a / 2, rows 64 (a % 2) + cc, K-group
                         // par; Y: slice a is B rows a Q .. a Q + Q - 1
                         const int off =
-                            isx ? (a >> 1) * S::kPairA + par * S::kLboA +
-                                      ((64 * (a & 1) + cc) >> 3) * 128 + (cc & 7) * 16
-                                : S::kOffB + par * S::kLboB + ((a * Q + cc) >> 3) * 128 +
-                                      (cc & 7) * 16;
+                            isxc[cb] ? (a >> 1) * S::kPairA + par * S::kLboA +
+                                           ((64 * (a & 1) + cc) >> 3) * 128 + (cc & 7) * 16
+                                     : S::kOffB + par * S::kLboB + ((a * Q + cc) >> 3) * 128 +
+                                           (cc & 7) * 16;
                         *reinterpret_cast<uint4*>(st + off) = v;
                     }
                 }
@@ -844,11 +899,36 @@ k_oz_gram(MB<const double> X, MB<const double> Y, int64_t n, double* __restrict_
         const bool upper = qd < 2;
         const int p = (qd & 1) * 32 + lane;
         const bool own = p < P;
-        // this thread converts columns c0 .. c0 + QH - 1 and sends the other half
-        const int c0 = upper ? 0 : QH;
+        // this thread converts columns c0 .. c0 + QH - 1 and hands s0 .. s0 + QH - 1 over
+        const int c0 = upper ? 0 : QH, s0 = upper ? QH : 0;
+        // exchange buffers [column][row]: a warp's 32 rows are 32 consecutive words
         long long* xsend = reinterpret_cast<long long*>(sm + S::kOffXch + (upper ? 0 : S::kXch));
         const long long* xrecv =
             reinterpret_cast<const long long*>(sm + S::kOffXch + (upper ? S::kXch : 0));
+        const uint32_t lane_base = tbase + ((uint32_t)(qd * 32) << 16);
+        // nine group sums of 4 columns from col, combined (block j holds group j + 2 in the
+        // upper lanes and group j + 3 in the lower ones; group 2 is upper only)
+        auto combine4 = [&](uint32_t taddr, long long (&v)[4]) {
+            float g[kGroups][4];
+            if (upper) {
+#pragma unroll
+                for (int j = 0; j < kGroups; ++j) tmem_ld4(taddr + (uint32_t)(j * Q), g[j]);
+            } else {
+#pragma unroll
+                for (int u = 0; u < 4; ++u) g[0][u] = 0.f;
+#pragma unroll
+                for (int j = 0; j + 1 < kGroups; ++j)
+                    tmem_ld4(taddr + (uint32_t)(j * Q), g[j + 1]);
+            }
+            tmem_wait_ld();
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                float gu[kGroups];
+#pragma unroll
+                for (int gi = 0; gi < kGroups; ++gi) gu[gi] = g[gi][u];
+                v[u] = combine_groups(gu);
+            }
+        };
         double acc[QH];
 #pragma unroll
         for (int q = 0; q < QH; ++q) acc[q] = 0.0;
@@ -860,55 +940,52 @@ k_oz_gram(MB<const double> X, MB<const double> Y, int64_t n, double* __restrict_
             // the four epilogue warps share named barrier 2: they leave together
             if (bar_or(2, 128, !ok || abort_flag)) break;
             tc_fence_after();
-            const int ep = own ? cexp[buf][p] : 0;
-            int fq[QH];
+            const uint32_t taddr = lane_base + (uint32_t)set * S::kAcc;
+            // the partner's half: its first 8 columns straight into the exchange buffer, the
+            // rest (Q = 32) into registers for the second round
+            constexpr int R2 = QH > 8 ? QH - 8 : 0;
+            long long Vs[R2 > 0 ? R2 : 1];
 #pragma unroll
-            for (int q = 0; q < QH; ++q) fq[q] = cexp[buf][P + c0 + q];
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&cexp_empty[buf]);
-            const uint32_t taddr = tbase + ((uint32_t)(qd * 32) << 16) + (uint32_t)set * S::kAcc;
-            long long V[Q];
-#pragma unroll
-            for (int col0 = 0; col0 < Q; col0 += 4) {
-                float g[kGroups][4];
-                if (upper) {
-#pragma unroll
-                    for (int j = 0; j < kGroups; ++j)
-                        tmem_ld4(taddr + (uint32_t)(j * Q + col0), g[j]);
-                } else {
-                    // block j holds group j + 3: group index j + 1; group 2 is upper only
-#pragma unroll
-                    for (int u = 0; u < 4; ++u) g[0][u] = 0.f;
-#pragma unroll
-                    for (int j = 0; j + 1 < kGroups; ++j)
-                        tmem_ld4(taddr + (uint32_t)(j * Q + col0), g[j + 1]);
-                }
-                tmem_wait_ld();
+            for (int k = 0; k < QH; k += 4) {
+                long long v[4];
+                combine4(taddr + (uint32_t)(s0 + k), v);
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
-                    float gu[kGroups];
-#pragma unroll
-                    for (int gi = 0; gi < kGroups; ++gi) gu[gi] = g[gi][u];
-                    V[col0 + u] = combine_groups(gu);
+                    if (k + u < 8)
+                        xsend[(k + u) * 64 + p] = v[u];
+                    else
+                        Vs[k + u - 8] = v[u];
                 }
+            }
+            long long V[QH];
+#pragma unroll
+            for (int k = 0; k < QH; k += 4) {
+                long long v[4];
+                combine4(taddr + (uint32_t)(c0 + k), v);
+#pragma unroll
+                for (int u = 0; u < 4; ++u) V[k + u] = v[u];
             }
             // the accumulator is read: the MMA warp may start the next tile in it
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&acc_empty[set]);
-            // (register arrays indexed with constants only: the halves are selected per lane)
-            long long mine[QH];
-#pragma unroll
-            for (int q = 0; q < QH; ++q) {
-                xsend[p * QH + q] = upper ? V[QH + q] : V[q];
-                mine[q] = upper ? V[q] : V[QH + q];
-            }
             asm volatile("bar.sync 2, 128;" ::: "memory");
 #pragma unroll
-            for (int q = 0; q < QH; ++q) {
-                const long long v = mine[q] + xrecv[p * QH + q];
-                acc[q] = fma((double)v, pow2_biased(ep + fq[q] - 1077), acc[q]);
+            for (int q = 0; q < 8 && q < QH; ++q) V[q] += xrecv[q * 64 + p];
+            if (R2 > 0) {
+                asm volatile("bar.sync 2, 128;" ::: "memory");   // round 1 read everywhere
+#pragma unroll
+                for (int q = 0; q < R2; ++q) xsend[q * 64 + p] = Vs[q];
+                asm volatile("bar.sync 2, 128;" ::: "memory");
+#pragma unroll
+                for (int q = 0; q < R2; ++q) V[8 + q] += xrecv[q * 64 + p];
             }
+            const int ep = own ? cexp[buf][p] : 0;
+#pragma unroll
+            for (int q = 0; q < QH; ++q)
+                acc[q] = fma((double)V[q], pow2_biased(ep + cexp[buf][P + c0 + q] - 1077), acc[q]);
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&cexp_empty[buf]);
             asm volatile("bar.sync 2, 128;" ::: "memory");   // exchange buffers reusable
         }
         if (own) {
