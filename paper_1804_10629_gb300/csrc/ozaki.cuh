@@ -188,6 +188,36 @@ __device__ __forceinline__ uint32_t pack_bf16(uint32_t f0, uint32_t f1) {
     return __byte_perm(f0, f1, 0x7632);
 }
 
+// Byte slices (the Gram): slice a (0-based) is byte 7 - a of F (bits 56 - 8a .. 63 - 8a;
+// slice 0 below 2^7, the others below 2^8), placed in the low byte of the pattern of the
+// float 2^23 (sign folded in) by one byte permutation; adding -+2^23 leaves exactly +-s.
+__device__ __forceinline__ uint32_t byte_slice_bits(uint64_t F, int a, uint32_t ms, float undo) {
+    const uint32_t hi = (uint32_t)(F >> 32), lo = (uint32_t)F;
+    uint32_t w;
+    switch (a) {
+        case 0: w = __byte_perm(hi, ms, 0x7653); break;
+        case 1: w = __byte_perm(hi, ms, 0x7652); break;
+        case 2: w = __byte_perm(hi, ms, 0x7651); break;
+        case 3: w = __byte_perm(hi, ms, 0x7650); break;
+        case 4: w = __byte_perm(lo, ms, 0x7653); break;
+        case 5: w = __byte_perm(lo, ms, 0x7652); break;
+        case 6: w = __byte_perm(lo, ms, 0x7651); break;
+        default: w = __byte_perm(lo, ms, 0x7650); break;
+    }
+    return __float_as_uint(__uint_as_float(w) + undo);
+}
+// the eight exact byte-pair group sums G_2 .. G_9 combined into V >> 16 with
+// V = sum_g G_g 2^{8(9-g)} (|G_g| < 2^24, |G_2| < 2^21: hi = G_2..G_5 below 2^45,
+// lo = G_6..G_9 below 2^51, the result below 2^62)
+__device__ __forceinline__ long long combine_byte_groups(const float (&g)[8]) {
+    long long hi = 0, lo = 0;
+#pragma unroll
+    for (int gi = 0; gi < 4; ++gi) hi = hi * 256 + (long long)__float2int_rn(g[gi]);
+#pragma unroll
+    for (int gi = 4; gi < 8; ++gi) lo = lo * 256 + (long long)__float2int_rn(g[gi]);
+    return hi * (1ll << 16) + (lo >> 16);
+}
+
 // 16-byte global -> shared copy by this thread (cp.async); src_bytes 0 writes zeros
 __device__ __forceinline__ void cp_async16_zfill(void* dst, const void* src, uint32_t src_bytes) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(bulk::smem_addr(dst)),
@@ -216,9 +246,10 @@ __device__ __forceinline__ void cp_async16_zfill(void* dst, const void* src, uin
 // shared abort word that every role checks, so all roles leave their loops.
 constexpr int kSlicerWarps = 8;
 constexpr int kMmaWarp = 8;
-constexpr int kEpiWarp0 = 9;
-constexpr int kPrefetchWarp = 13;
-constexpr int kUpdThreads = 14 * 32;
+constexpr int kPrefetchWarp = 9;
+constexpr int kEpiWarp0 = 10;
+constexpr int kEpiWarps = 8;
+constexpr int kUpdThreads = (kEpiWarp0 + kEpiWarps) * 32;
 constexpr int kPrefetchAhead = 2;   // tiles of lead of the L2 prefetch
 constexpr int kKS = 16;          // columns of X per ring stage (one MMA K-step)
 constexpr int kStages = 3;
@@ -341,9 +372,9 @@ k_oz_update(MB<const double> X, const double* __restrict__ C, MB<const double> Y
         }
         for (int b = 0; b < 2; ++b) {
             bulk::mbar_init(&acc_full[b], 1);
-            bulk::mbar_init(&acc_empty[b], 4);
+            bulk::mbar_init(&acc_empty[b], kEpiWarps);
             bulk::mbar_init(&erow_full[b], kSlicerWarps);
-            bulk::mbar_init(&erow_empty[b], 4);
+            bulk::mbar_init(&erow_empty[b], kEpiWarps);
         }
         bulk::mbar_init(&fin, 1);
         abort_flag = 0;
@@ -527,68 +558,69 @@ k_oz_update(MB<const double> X, const double* __restrict__ C, MB<const double> Y
         }
         __syncwarp();
     } else {
-        // ---- epilogue: quarter qd = warp % 4, rows 32 qd + lane of the tile
+        // ---- epilogue: quarter qd = warp % 4, rows 32 qd + lane of the tile, columns
+        //      c0 .. c0 + Q / 2 - 1
+        constexpr int QH = Q / 2;
         const int qd = warp & 3;
         const int m = qd * 32 + lane;
-        // Y values of 8 columns of this thread's row (zero past n or without Y)
-        auto load_y = [&](int64_t ri, int col0, double (&yv)[8]) {
-            if (beta_on && ri < n) {
-                const double2* yr = reinterpret_cast<const double2*>(Y.blk(0) + ri * Y.w + col0);
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const double2 v = yr[u];
-                    yv[2 * u] = v.x;
-                    yv[2 * u + 1] = v.y;
-                }
-            } else {
-#pragma unroll
-                for (int u = 0; u < 8; ++u) yv[u] = 0.0;
-            }
-        };
+        const int c0 = ((warp - kEpiWarp0) >> 2) * QH;
         int lt = 0;
         for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++lt) {
             const int buf = lt & 1, set = lt % S::kSets;
             const int64_t ri = tile * kTile + m;
-            // the first Y columns are requested before the accumulator is ready
-            double ynext[8];
-            load_y(ri, 0, ynext);
             if (!wait_or_abort(&acc_full[set], (lt / S::kSets) & 1, &abort_flag)) break;
             if (!wait_or_abort(&erow_full[buf], (lt >> 1) & 1, &abort_flag)) break;
             tc_fence_after();
             const int er = erow[buf][m];
             __syncwarp();
             if (lane == 0) mbar_arrive(&erow_empty[buf]);
-            const uint32_t taddr = tbase + ((uint32_t)(qd * 32) << 16) + (uint32_t)set * S::kAcc;
-#pragma unroll 1
-            for (int col0 = 0; col0 < Q; col0 += 8) {
-                double yv[8];
+            const uint32_t taddr = tbase + ((uint32_t)(qd * 32) << 16) + (uint32_t)set * S::kAcc +
+                                   (uint32_t)c0;
+            long long V[QH];
 #pragma unroll
-                for (int u = 0; u < 8; ++u) yv[u] = ynext[u];
-                if (col0 + 8 < Q) load_y(ri, col0 + 8, ynext);   // one chunk ahead
-                float g[kGroups][8];
+            for (int k = 0; k < QH; k += 4) {
+                float g[kGroups][4];
 #pragma unroll
                 for (int gi = 0; gi < kGroups; ++gi)
-                    tmem_ld8(taddr + (uint32_t)(gi * Q + col0), g[gi]);
+                    tmem_ld4(taddr + (uint32_t)(gi * Q + k), g[gi]);
                 tmem_wait_ld();
-                if (ri < n) {
-                    double ov[8];
 #pragma unroll
-                    for (int u = 0; u < 8; ++u) {
-                        float gu[kGroups];
+                for (int u = 0; u < 4; ++u) {
+                    float gu[kGroups];
 #pragma unroll
-                        for (int gi = 0; gi < kGroups; ++gi) gu[gi] = g[gi][u];
-                        const long long v = combine_groups(gu);
-                        const double scale = pow2_biased(er + fcol[col0 + u] - 1077);
-                        ov[u] = fma((double)(beta_on ? -v : v), scale, yv[u]);
-                    }
-                    double2* orow = reinterpret_cast<double2*>(OUT.blk(0) + ri * OUT.w + col0);
-#pragma unroll
-                    for (int u = 0; u < 4; ++u) orow[u] = make_double2(ov[2 * u], ov[2 * u + 1]);
+                    for (int gi = 0; gi < kGroups; ++gi) gu[gi] = g[gi][u];
+                    V[k + u] = combine_groups(gu);
                 }
             }
+            // the accumulator is read: the MMA warp may start the next tile in it
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&acc_empty[set]);
+            if (ri < n) {
+#pragma unroll
+                for (int k = 0; k < QH; k += 4) {
+                    double yv[4] = {0.0, 0.0, 0.0, 0.0};
+                    if (beta_on) {
+                        const double2* yr =
+                            reinterpret_cast<const double2*>(Y.blk(0) + ri * Y.w + c0 + k);
+                        const double2 a = yr[0], b = yr[1];
+                        yv[0] = a.x;
+                        yv[1] = a.y;
+                        yv[2] = b.x;
+                        yv[3] = b.y;
+                    }
+                    double ov[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const long long v = V[k + u];
+                        const double scale = pow2_biased(er + fcol[c0 + k + u] - 1077);
+                        ov[u] = fma((double)(beta_on ? -v : v), scale, yv[u]);
+                    }
+                    double2* orow = reinterpret_cast<double2*>(OUT.blk(0) + ri * OUT.w + c0 + k);
+                    orow[0] = make_double2(ov[0], ov[1]);
+                    orow[1] = make_double2(ov[2], ov[3]);
+                }
+            }
         }
     }
     __syncthreads();
@@ -603,20 +635,25 @@ k_oz_update(MB<const double> X, const double* __restrict__ C, MB<const double> Y
 // C = X^T Y over the n rows (CGS coefficients Q^T (A W), the A-CholQR Gram W^T (A W)):
 // X n x P (P <= 64), Y n x Q (Q = 16 or 32).  The contraction runs over rows, in tiles of 64
 // rows: every column of X and of Y is scaled by its binade over the tile (e_p, f_q), and
-// the epilogue adds the tile's (V >> 14) 2^{e_p + f_q - 2100} into a float64 accumulator
-// per output held in registers across the CTA's tiles.  Each CTA writes its P x Q partial
-// sum; k_gram_reduce adds the partials in CTA order.
+// cut into eight byte slices of the same 63-bit fixed-point magnitude F (slice a, 1-based,
+// holds bits 64 - 8a .. 71 - 8a; bf16 holds every byte exactly).  The 36 slice pairs with
+// a + b <= 9 form eight groups g = 2..9; the epilogue adds the tile's
+// (V >> 16) 2^{e_p + f_q - 2098}, V = sum_g G_g 2^{8(9-g)}, into a float64 accumulator per
+// output held in registers across the CTA's tiles (the dropped pairs and the truncation of
+// F weigh at most about 2^-60 of the product of the column maxima per term).  Each CTA
+// writes its P x Q partial sum; k_gram_reduce adds the partials in CTA order.
 //
 // Slice pairs in M: the A operand of one MMA holds two X slices, a (rows 0-63, X column p
 // in row p) and a + 1 (rows 64-127), so every MMA runs at M = 128.  The MMA of the pair
-// (a, a + 1), a odd, multiplies by the Y slices 1 .. 10 - a stacked along N and starts at
+// (a, a + 1), a odd, multiplies by the Y slices 1 .. 9 - a stacked along N and starts at
 // the accumulator columns of group a + 1: tensor-memory lanes 0-63 receive the pairs (a, b)
 // in the columns of group a + b, lanes 64-127 the pairs (a + 1, b) in the columns of group
 // a + b as well, that is group (a + 1 + b) - 1.  So column block j holds group j + 2 in the
-// upper lanes and group j + 3 in the lower lanes (block 8 of the lower lanes, group 11, is
-// beyond the 45 pairs and not read).  A group of one half holds at most five pairs, so its
-// fp32 sum stays exact (5 x 64 rows x 127^2 < 2^24).  Five MMAs per K-step (slice 10 is
-// zero) instead of nine at M = 64.
+// upper lanes and group j + 3 in the lower lanes (block 7 of the lower lanes, group 10, is
+// beyond the 36 pairs and not read).  A group of one half holds at most four pairs, so its
+// fp32 sum stays exact (4 x 64 rows x 255^2 < 2^24).  Four MMAs per K-step; an accumulator
+// set is 8 Q columns, so two sets fit in tensor memory and the MMAs of one tile overlap the
+// epilogue of the previous one.
 //
 //   warps 0-7  (slicers): warp w cuts row group w of the tile (rows 8 w .. 8 w + 7), lane =
 //              column within each 32-column block of X | Y; pass 1 takes the column
@@ -624,25 +661,29 @@ k_oz_update(MB<const double> X, const double* __restrict__ C, MB<const double> Y
 //              eight row groups), pass 2 writes the warp's 8 rows of every slice into the
 //              stage of its K-step (w / 2), K-group w % 2.  Two slicer warps per SM
 //              sub-partition;
-//   warp 8     (MMA): per K-step the five pair MMAs (M = 128, K = 16, N in pieces <= 256);
+//   warp 8     (MMA): per K-step the four pair MMAs (M = 128, K = 16, N in pieces <= 256);
 //   warp 9     (producer): one thread copies the tile's rows of every X block and of Y
 //              (contiguous runs of 64 x w doubles) into one of two raw shared buffers with
 //              bulk copies completing on an mbarrier, one tile ahead of the slicers;
-//   warps 10-13 (epilogue): warp w reads lane quarter q = w % 4 of the accumulator; the
-//              thread for output row p = 32 (q & 1) + lane holds the upper groups (q < 2,
-//              lanes 0-63) or the lower groups (q >= 2, lanes 64-127) of that row.  It
-//              combines the half of the columns its partner (same row, other half)
-//              converts and leaves it in shared memory, combines its own half, releases the
-//              accumulator to the MMA warp, adds the partner's values and converts and
-//              scales Q / 2 outputs.
+//   warps 10-17 (epilogue): warp w reads lane quarter q = w % 4 of the accumulator, for
+//              the columns of half (w - 10) / 4 of C; the thread for output row
+//              p = 32 (q & 1) + lane holds the upper groups (q < 2, lanes 0-63) or the lower
+//              groups (q >= 2, lanes 64-127) of that row.  It combines its groups of its
+//              Q / 2 columns, releases the accumulator to the MMA warp, then converts and
+//              scales them into float64 accumulators of its own; the upper and lower
+//              accumulators of an output are added once, at the end.
 constexpr int kGramSlicers = 8;
 constexpr int kGramMmaWarp = 8;
 constexpr int kGramProducerWarp = 9;
 constexpr int kGramEpiWarp0 = 10;
-constexpr int kGramThreads = 14 * 32;
+constexpr int kGramEpiWarps = 8;
+constexpr int kGramThreads = (kGramEpiWarp0 + kGramEpiWarps) * 32;
+constexpr int kGramCexp = 3;         // tile binade buffers (the epilogue frees one late)
 constexpr int kGramRows = 64;        // rows per tile (binade scope, exact fp32 sums)
 constexpr int kGramStages = 4;      // one tile of K-steps: no stage is reused within a tile
-constexpr int kPairs = (kSlices + 1) / 2;   // X slice pairs per K-step (the last one half zero)
+constexpr int kGSlices = 8;          // byte slices of the 63-bit fixed-point magnitude
+constexpr int kGGroups = 8;          // byte-pair groups g = a + b = 2..9
+constexpr int kPairs = kGSlices / 2; // X slice pairs per K-step
 
 template <int P, int Q>
 struct GramShape {
@@ -651,18 +692,17 @@ struct GramShape {
     static constexpr int kM = 128;                                 // MMA M (slice pair)
     static constexpr int kPairA = kM * kKS * 2;                    // 4 KB: one slice pair
     static constexpr int kSliceB = Q * kKS * 2;
-    static constexpr int kStageBytes = kPairs * kPairA + kSlices * kSliceB;
+    static constexpr int kStageBytes = kPairs * kPairA + kGSlices * kSliceB;
     static constexpr int kOffB = kPairs * kPairA;                  // B inside a stage
     static constexpr int kRawX = kGramRows * P * 8;                // raw X tile, bytes
     static constexpr int kRawY = kGramRows * Q * 8;
     static constexpr int kOffRaw = kGramStages * kStageBytes;      // raw buffers after ring
-    static constexpr int kXch = 64 * 8 * 8;                        // one direction, 8 columns
-    static constexpr int kOffXch = kOffRaw + 2 * (kRawX + kRawY);
-    static constexpr int kSmem = kOffXch + 2 * kXch + 1024;
+    static constexpr int kSmem = kOffRaw + 2 * (kRawX + kRawY) + 1024;
     static constexpr int kLboA = (kM / 8) * 128;                   // 2 KB
-    static constexpr int kLboB = (kSlices * Q / 8) * 128;          // Y slices stacked in N
-    static constexpr uint32_t kAcc = (uint32_t)(kGroups * Q);
+    static constexpr int kLboB = (kGSlices * Q / 8) * 128;         // Y slices stacked in N
+    static constexpr uint32_t kAcc = (uint32_t)(kGGroups * Q);
     static constexpr int kSets = 2 * kAcc <= 512 ? 2 : 1;          // accumulator sets
+    static_assert(kSets == 2, "two accumulator sets");
     static constexpr uint32_t kCols = 512;
     static constexpr int kT = P + Q;                               // columns sliced per row
     static constexpr int kNB = (kT + 31) / 32;                     // column blocks
@@ -681,10 +721,11 @@ k_oz_gram(MB<const double> X, MB<const double> Y, int64_t n, double* __restrict_
     extern __shared__ __align__(1024) unsigned char oz_raw[];
     unsigned char* sm = oz_raw + ((1024 - (bulk::smem_addr(oz_raw) & 1023)) & 1023);
     __shared__ __align__(8) uint64_t full[kGramStages], empty[kGramStages];
-    __shared__ __align__(8) uint64_t acc_full[2], acc_empty[2], cexp_full[2], cexp_empty[2], fin;
+    __shared__ __align__(8) uint64_t acc_full[2], acc_empty[2], fin;
+    __shared__ __align__(8) uint64_t cexp_full[kGramCexp], cexp_empty[kGramCexp];
     __shared__ __align__(8) uint64_t raw_full[2], raw_empty[2];
     __shared__ uint32_t tslot;
-    __shared__ int cexp[2][S::kT];                    // tile binades: X columns, then Y
+    __shared__ int cexp[kGramCexp][S::kT];            // tile binades: X columns, then Y
     __shared__ int cmax[kGramSlicers][S::kNB * 32];   // per row group, pass 1
     __shared__ volatile int abort_flag;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -702,11 +743,13 @@ k_oz_gram(MB<const double> X, MB<const double> Y, int64_t n, double* __restrict_
         }
         for (int b = 0; b < 2; ++b) {
             bulk::mbar_init(&acc_full[b], 1);
-            bulk::mbar_init(&acc_empty[b], 4);
-            bulk::mbar_init(&cexp_full[b], kGramSlicers);
-            bulk::mbar_init(&cexp_empty[b], 4);
+            bulk::mbar_init(&acc_empty[b], kGramEpiWarps);
             bulk::mbar_init(&raw_full[b], 1);
             bulk::mbar_init(&raw_empty[b], kGramSlicers);
+        }
+        for (int b = 0; b < kGramCexp; ++b) {
+            bulk::mbar_init(&cexp_full[b], kGramSlicers);
+            bulk::mbar_init(&cexp_empty[b], kGramEpiWarps);
         }
         bulk::mbar_init(&fin, 1);
         abort_flag = 0;
@@ -743,9 +786,10 @@ k_oz_gram(MB<const double> X, MB<const double> Y, int64_t n, double* __restrict_
         int lt = 0;
         bool failed = false;   // the slicer warps leave together (they share named barriers)
         for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++lt) {
-            const int buf = lt & 1;   // binade / raw buffer (two tiles in flight)
-            if (lt >= 2 && !failed &&
-                !wait_or_abort(&cexp_empty[buf], ((lt >> 1) - 1) & 1, &abort_flag))
+            const int buf = lt & 1;                    // raw buffer (two tiles in flight)
+            const int cb3 = lt % kGramCexp;            // binade buffer
+            if (lt >= kGramCexp && !failed &&
+                !wait_or_abort(&cexp_empty[cb3], ((lt / kGramCexp) - 1) & 1, &abort_flag))
                 failed = true;
             if (!failed && !wait_or_abort(&raw_full[buf], (lt >> 1) & 1, &abort_flag))
                 failed = true;
@@ -773,11 +817,11 @@ k_oz_gram(MB<const double> X, MB<const double> Y, int64_t n, double* __restrict_
 #pragma unroll
                 for (int r = 0; r < kGramSlicers; ++r) m = max(m, cmax[r][cb * 32 + lane]);
                 e[cb] = m;
-                if (rg == 0 && act[cb]) cexp[buf][cb * 32 + lane] = m;
+                if (rg == 0 && act[cb]) cexp[cb3][cb * 32 + lane] = m;
             }
             asm volatile("bar.sync 1, %0;" ::"r"(kGramSlicers * 32) : "memory");
             __syncwarp();
-            if (lane == 0) mbar_arrive(&cexp_full[buf]);
+            if (lane == 0) mbar_arrive(&cexp_full[cb3]);
             // pass 2: this row group's 8 rows of every slice, into the stage of K-step ks
             const int stage = lt * S::kKSteps + ks;
             const int slot = stage % kGramStages, use = stage / kGramStages;
@@ -802,16 +846,16 @@ k_oz_gram(MB<const double> X, MB<const double> Y, int64_t n, double* __restrict_
                         undo[u] = sign_undo(neg);
                     }
 #pragma unroll
-                    for (int a = 0; a < kSlices; ++a) {
+                    for (int a = 0; a < kGSlices; ++a) {
                         uint4 v;
-                        v.x = pack_bf16(slice_bits(F[0], a, ms[0], undo[0]),
-                                        slice_bits(F[1], a, ms[1], undo[1]));
-                        v.y = pack_bf16(slice_bits(F[2], a, ms[2], undo[2]),
-                                        slice_bits(F[3], a, ms[3], undo[3]));
-                        v.z = pack_bf16(slice_bits(F[4], a, ms[4], undo[4]),
-                                        slice_bits(F[5], a, ms[5], undo[5]));
-                        v.w = pack_bf16(slice_bits(F[6], a, ms[6], undo[6]),
-                                        slice_bits(F[7], a, ms[7], undo[7]));
+                        v.x = pack_bf16(byte_slice_bits(F[0], a, ms[0], undo[0]),
+                                        byte_slice_bits(F[1], a, ms[1], undo[1]));
+                        v.y = pack_bf16(byte_slice_bits(F[2], a, ms[2], undo[2]),
+                                        byte_slice_bits(F[3], a, ms[3], undo[3]));
+                        v.z = pack_bf16(byte_slice_bits(F[4], a, ms[4], undo[4]),
+                                        byte_slice_bits(F[5], a, ms[5], undo[5]));
+                        v.w = pack_bf16(byte_slice_bits(F[6], a, ms[6], undo[6]),
+                                        byte_slice_bits(F[7], a, ms[7], undo[7]));
                         // X: slice a (0-based) in pair a / 2, rows 64 (a % 2) + cc, K-group
                         // par; Y: slice a is B rows a Q .. a Q + Q - 1
                         const int off =
@@ -873,7 +917,7 @@ k_oz_gram(MB<const double> X, MB<const double> Y, int64_t n, double* __restrict_
                     for (int j = 0; j < kPairs; ++j) {
                         const int a = 2 * j + 1;                  // 1-based upper slice
                         const uint64_t ad = smem_desc(st + j * S::kPairA, S::kLboA, 128);
-                        const int na = (kGroups + 1 - a) * Q;
+                        const int na = (kGSlices + 1 - a) * Q;   // Y slices 1 .. 9 - a
 #pragma unroll
                         for (int n0 = 0; n0 < na; n0 += kMaxN) {
                             const int nn = (na - n0) < kMaxN ? (na - n0) : kMaxN;
@@ -894,104 +938,72 @@ k_oz_gram(MB<const double> X, MB<const double> Y, int64_t n, double* __restrict_
         }
         __syncwarp();
     } else if (warp >= kGramEpiWarp0) {
-        // ---- epilogue: row p = 32 (qd & 1) + lane; upper groups (qd < 2) or lower (qd >= 2)
+        // ---- epilogue: row p = 32 (qd & 1) + lane; upper groups (qd < 2) or lower (qd >= 2);
+        //      columns c0 .. c0 + QH - 1
         const int qd = warp & 3;
         const bool upper = qd < 2;
         const int p = (qd & 1) * 32 + lane;
         const bool own = p < P;
-        // this thread converts columns c0 .. c0 + QH - 1 and hands s0 .. s0 + QH - 1 over
-        const int c0 = upper ? 0 : QH, s0 = upper ? QH : 0;
-        // exchange buffers [column][row]: a warp's 32 rows are 32 consecutive words
-        long long* xsend = reinterpret_cast<long long*>(sm + S::kOffXch + (upper ? 0 : S::kXch));
-        const long long* xrecv =
-            reinterpret_cast<const long long*>(sm + S::kOffXch + (upper ? S::kXch : 0));
-        const uint32_t lane_base = tbase + ((uint32_t)(qd * 32) << 16);
-        // nine group sums of 4 columns from col, combined (block j holds group j + 2 in the
-        // upper lanes and group j + 3 in the lower ones; group 2 is upper only)
-        auto combine4 = [&](uint32_t taddr, long long (&v)[4]) {
-            float g[kGroups][4];
-            if (upper) {
-#pragma unroll
-                for (int j = 0; j < kGroups; ++j) tmem_ld4(taddr + (uint32_t)(j * Q), g[j]);
-            } else {
-#pragma unroll
-                for (int u = 0; u < 4; ++u) g[0][u] = 0.f;
-#pragma unroll
-                for (int j = 0; j + 1 < kGroups; ++j)
-                    tmem_ld4(taddr + (uint32_t)(j * Q), g[j + 1]);
-            }
-            tmem_wait_ld();
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                float gu[kGroups];
-#pragma unroll
-                for (int gi = 0; gi < kGroups; ++gi) gu[gi] = g[gi][u];
-                v[u] = combine_groups(gu);
-            }
-        };
+        const int c0 = ((warp - kGramEpiWarp0) >> 2) * QH;
+        const uint32_t lane_base = tbase + ((uint32_t)(qd * 32) << 16) + (uint32_t)c0;
         double acc[QH];
 #pragma unroll
         for (int q = 0; q < QH; ++q) acc[q] = 0.0;
         int lt = 0;
         for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++lt) {
-            const int buf = lt & 1, set = lt % S::kSets;
-            bool ok = wait_or_abort(&acc_full[set], (lt / S::kSets) & 1, &abort_flag);
-            ok = ok && wait_or_abort(&cexp_full[buf], (lt >> 1) & 1, &abort_flag);
-            // the four epilogue warps share named barrier 2: they leave together
-            if (bar_or(2, 128, !ok || abort_flag)) break;
+            const int set = lt % S::kSets, cb3 = lt % kGramCexp;
+            if (!wait_or_abort(&acc_full[set], (lt / S::kSets) & 1, &abort_flag)) break;
+            if (!wait_or_abort(&cexp_full[cb3], (lt / kGramCexp) & 1, &abort_flag)) break;
             tc_fence_after();
             const uint32_t taddr = lane_base + (uint32_t)set * S::kAcc;
-            // the partner's half: its first 8 columns straight into the exchange buffer, the
-            // rest (Q = 32) into registers for the second round
-            constexpr int R2 = QH > 8 ? QH - 8 : 0;
-            long long Vs[R2 > 0 ? R2 : 1];
-#pragma unroll
-            for (int k = 0; k < QH; k += 4) {
-                long long v[4];
-                combine4(taddr + (uint32_t)(s0 + k), v);
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    if (k + u < 8)
-                        xsend[(k + u) * 64 + p] = v[u];
-                    else
-                        Vs[k + u - 8] = v[u];
-                }
-            }
+            // block j holds group j + 2 in the upper lanes and group j + 3 in the lower ones
             long long V[QH];
 #pragma unroll
             for (int k = 0; k < QH; k += 4) {
-                long long v[4];
-                combine4(taddr + (uint32_t)(c0 + k), v);
+                float g[kGGroups][4];
+                if (upper) {
 #pragma unroll
-                for (int u = 0; u < 4; ++u) V[k + u] = v[u];
+                    for (int j = 0; j < kGGroups; ++j)
+                        tmem_ld4(taddr + (uint32_t)(j * Q + k), g[j]);
+                } else {
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) g[0][u] = 0.f;
+#pragma unroll
+                    for (int j = 0; j + 1 < kGGroups; ++j)
+                        tmem_ld4(taddr + (uint32_t)(j * Q + k), g[j + 1]);
+                }
+                tmem_wait_ld();
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    float gu[kGGroups];
+#pragma unroll
+                    for (int gi = 0; gi < kGGroups; ++gi) gu[gi] = g[gi][u];
+                    V[k + u] = combine_byte_groups(gu);
+                }
             }
             // the accumulator is read: the MMA warp may start the next tile in it
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&acc_empty[set]);
-            asm volatile("bar.sync 2, 128;" ::: "memory");
-#pragma unroll
-            for (int q = 0; q < 8 && q < QH; ++q) V[q] += xrecv[q * 64 + p];
-            if (R2 > 0) {
-                asm volatile("bar.sync 2, 128;" ::: "memory");   // round 1 read everywhere
-#pragma unroll
-                for (int q = 0; q < R2; ++q) xsend[q * 64 + p] = Vs[q];
-                asm volatile("bar.sync 2, 128;" ::: "memory");
-#pragma unroll
-                for (int q = 0; q < R2; ++q) V[8 + q] += xrecv[q * 64 + p];
-            }
-            const int ep = own ? cexp[buf][p] : 0;
+            const int ep = own ? cexp[cb3][p] : 0;
 #pragma unroll
             for (int q = 0; q < QH; ++q)
-                acc[q] = fma((double)V[q], pow2_biased(ep + cexp[buf][P + c0 + q] - 1077), acc[q]);
+                acc[q] = fma((double)V[q], pow2_biased(ep + cexp[cb3][P + c0 + q] - 1075), acc[q]);
             __syncwarp();
-            if (lane == 0) mbar_arrive(&cexp_empty[buf]);
-            asm volatile("bar.sync 2, 128;" ::: "memory");   // exchange buffers reusable
+            if (lane == 0) mbar_arrive(&cexp_empty[cb3]);
         }
-        if (own) {
+        // upper + lower accumulators of each output, through the (now idle) raw buffers:
+        // every tile's copies have landed and been cut before its accumulator was final
+        double* red = reinterpret_cast<double*>(sm + S::kOffRaw);   // [64 rows][Q]
+        if (!upper) {
+#pragma unroll
+            for (int q = 0; q < QH; ++q) red[p * Q + c0 + q] = acc[q];
+        }
+        asm volatile("bar.sync 2, %0;" ::"r"(kGramEpiWarps * 32) : "memory");
+        if (upper && own) {
             double* out = partials + (int64_t)blockIdx.x * 4096 + p * Q + c0;
 #pragma unroll
-            for (int q = 0; q < QH; ++q) out[q] = acc[q];
+            for (int q = 0; q < QH; ++q) out[q] = acc[q] + red[p * Q + c0 + q];
         }
     }
     __syncthreads();
