@@ -119,19 +119,33 @@ __device__ __forceinline__ void tmem_ld4(uint32_t taddr, float (&v)[4]) {
 #pragma unroll
     for (int i = 0; i < 4; ++i) v[i] = __uint_as_float(r[i]);
 }
+// 32 lanes x 2 consecutive 32-bit columns
+__device__ __forceinline__ void tmem_ld2(uint32_t taddr, float (&v)[2]) {
+    uint32_t r[2];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0, %1}, [%2];"
+                 : "=r"(r[0]), "=r"(r[1])
+                 : "r"(taddr)
+                 : "memory");
+    v[0] = __uint_as_float(r[0]);
+    v[1] = __uint_as_float(r[1]);
+}
 __device__ __forceinline__ void tmem_wait_ld() {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-// the nine exact group sums G_2 .. G_10 combined into V >> 14 with V = sum_g G_g 2^{7(10-g)}
-// (|G_g| < 2^24: hi = G_2..G_5 below 2^41, lo = G_6..G_10 below 2^52, the result below 2^62)
+// the nine exact group sums G_2 .. G_10 combined into about V >> 14, V = sum_g G_g 2^{7(10-g)}
+// (|G_g| < 2^24, |G_2| < 2^21): G_2 2^42 + G_3 2^35 + ... + G_8 + (G_9 >> 7) + (G_10 >> 14),
+// within two units of floor(V / 2^14), below 2^62.  The terms below 2^32 are added by
+// 32 x 32 -> 64-bit multiply-adds, the two top terms into the high word.
 __device__ __forceinline__ long long combine_groups(const float (&g)[kGroups]) {
-    long long hi = 0, lo = 0;
-#pragma unroll
-    for (int gi = 0; gi < 4; ++gi) hi = hi * 128 + (long long)__float2int_rn(g[gi]);
-#pragma unroll
-    for (int gi = 4; gi < kGroups; ++gi) lo = lo * 128 + (long long)__float2int_rn(g[gi]);
-    return hi * (1ll << 21) + (lo >> 14);
+    // each group converted where it is added: few registers live at a time
+    long long acc = (long long)(__float2int_rn(g[1]) * 8 + __float2int_rn(g[0]) * 1024) << 32;
+    acc += (long long)__float2int_rn(g[2]) * 268435456;
+    acc += (long long)__float2int_rn(g[3]) * 2097152;
+    acc += (long long)__float2int_rn(g[4]) * 16384;
+    acc += (long long)__float2int_rn(g[5]) * 128;
+    return acc + (__float2int_rn(g[6]) + (__float2int_rn(g[7]) >> 7) +
+                  (__float2int_rn(g[8]) >> 14));
 }
 // 2^{ex - 1023} for a biased exponent ex: 0 below the normal range, infinity above it
 __device__ __forceinline__ double pow2_biased(int ex) {
@@ -146,15 +160,23 @@ __device__ __forceinline__ int bexp(double x) {
     return (int)((__double_as_longlong(x) >> 52) & 0x7FF);
 }
 // 63-bit fixed-point magnitude of x against the binade 2^{e - 1022} (e >= bexp(x)):
-// floor(|x| 2^{63 - (e - 1022)}), below 2^63.
+// floor(|x| 2^{63 - (e - 1022)}) = (m << 10) >> (e - bexp(x)), m the 53-bit significand
+// with its leading bit; below 2^63.  Branch-free in 32-bit words (zero and subnormal values
+// shift out completely).
 __device__ __forceinline__ uint64_t fixed63(double x, int e) {
     const uint64_t u = (uint64_t)__double_as_longlong(x);
-    const int ex = (int)((u >> 52) & 0x7FF);
-    if (ex == 0) return 0;
-    const uint64_t m = (u & 0xFFFFFFFFFFFFFull) | (1ull << 52);
-    const int sh = ex - e + 10;   // <= 10
-    if (sh >= 0) return m << sh;
-    return (sh > -64) ? (m >> (-sh)) : 0;
+    const uint32_t hw = (uint32_t)(u >> 32), lw = (uint32_t)u;
+    const int ex = (int)((hw >> 20) & 0x7FF);
+    uint32_t h = __funnelshift_l(lw, (hw & 0xFFFFFu) | 0x100000u, 10);
+    uint32_t l = lw << 10;
+    int d = ex == 0 ? 64 : e - ex;
+    const bool big = d >= 32;   // a whole word first
+    l = big ? h : l;
+    h = big ? 0u : h;
+    d = big ? d - 32 : d;
+    l = __funnelshift_rc(l, h, (uint32_t)d);
+    h = d >= 32 ? 0u : (h >> (d & 31));
+    return ((uint64_t)h << 32) | l;
 }
 // bf16 bit pattern of the signed 7-bit slice: the float 2^23 + s (sign folded into the bit
 // pattern) plus -+2^23 is exactly +-s; its upper 16 bits are the bf16 value.
@@ -183,9 +205,16 @@ __device__ __forceinline__ uint32_t sign_magic(bool neg) {
     return 0x4B000000u | (neg ? 0x80000000u : 0u);
 }
 __device__ __forceinline__ float sign_undo(bool neg) { return neg ? 8388608.f : -8388608.f; }
-// two bf16 (the upper halves of two float bit patterns) in one word, first in the low half
+// the same -+2^23 from the magic pattern: its sign flipped
+__device__ __forceinline__ float undo_of(uint32_t magic_sign) {
+    return __uint_as_float(magic_sign ^ 0x80000000u);
+}
+// two bf16 in one word, first in the low half: the floats hold at most 8 significant bits,
+// so the conversion is exact
 __device__ __forceinline__ uint32_t pack_bf16(uint32_t f0, uint32_t f1) {
-    return __byte_perm(f0, f1, 0x7632);
+    uint32_t r;
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(__uint_as_float(f1)), "f"(__uint_as_float(f0)));
+    return r;
 }
 
 // Byte slices (the Gram): slice a (0-based) is byte 7 - a of F (bits 56 - 8a .. 63 - 8a;
@@ -206,16 +235,17 @@ __device__ __forceinline__ uint32_t byte_slice_bits(uint64_t F, int a, uint32_t 
     }
     return __float_as_uint(__uint_as_float(w) + undo);
 }
-// the eight exact byte-pair group sums G_2 .. G_9 combined into V >> 16 with
-// V = sum_g G_g 2^{8(9-g)} (|G_g| < 2^24, |G_2| < 2^21: hi = G_2..G_5 below 2^45,
-// lo = G_6..G_9 below 2^51, the result below 2^62)
+// the eight exact byte-pair group sums G_2 .. G_9 combined into about V >> 16,
+// V = sum_g G_g 2^{8(9-g)} (|G_g| < 2^24, |G_2| < 2^21): G_2 2^40 + G_3 2^32 + G_4 2^24 +
+// G_5 2^16 + G_6 2^8 + G_7 + (G_8 >> 8) + (G_9 >> 16), within two units of floor(V / 2^16),
+// below 2^62.
 __device__ __forceinline__ long long combine_byte_groups(const float (&g)[8]) {
-    long long hi = 0, lo = 0;
-#pragma unroll
-    for (int gi = 0; gi < 4; ++gi) hi = hi * 256 + (long long)__float2int_rn(g[gi]);
-#pragma unroll
-    for (int gi = 4; gi < 8; ++gi) lo = lo * 256 + (long long)__float2int_rn(g[gi]);
-    return hi * (1ll << 16) + (lo >> 16);
+    long long acc = (long long)(__float2int_rn(g[1]) + __float2int_rn(g[0]) * 256) << 32;
+    acc += (long long)__float2int_rn(g[2]) * 16777216;
+    acc += (long long)__float2int_rn(g[3]) * 65536;
+    acc += (long long)__float2int_rn(g[4]) * 256;
+    return acc + (__float2int_rn(g[5]) + (__float2int_rn(g[6]) >> 8) +
+                  (__float2int_rn(g[7]) >> 16));
 }
 
 // 16-byte global -> shared copy by this thread (cp.async); src_bytes 0 writes zeros
@@ -469,28 +499,26 @@ k_oz_update(MB<const double> X, const double* __restrict__ C, MB<const double> Y
                 }
                 uint64_t F[8];
                 uint32_t ms[8];
-                float undo[8];
 #pragma unroll
                 for (int u = 0; u < 8; ++u) {
                     const double x = xv[j * 8 + u];
                     F[u] = fixed63(x, e);
                     const bool neg = (__double_as_longlong(x) >> 63) != 0;
                     ms[u] = sign_magic(neg);
-                    undo[u] = sign_undo(neg);
                 }
                 unsigned char* dst = sm + slot * S::kStageBytes +
                                      (h * (kTile / 8) + (r >> 3)) * 128 + (r & 7) * 16;
 #pragma unroll
                 for (int a = 0; a < kSlices; ++a) {
                     uint4 v;
-                    v.x = pack_bf16(slice_bits(F[0], a, ms[0], undo[0]),
-                                    slice_bits(F[1], a, ms[1], undo[1]));
-                    v.y = pack_bf16(slice_bits(F[2], a, ms[2], undo[2]),
-                                    slice_bits(F[3], a, ms[3], undo[3]));
-                    v.z = pack_bf16(slice_bits(F[4], a, ms[4], undo[4]),
-                                    slice_bits(F[5], a, ms[5], undo[5]));
-                    v.w = pack_bf16(slice_bits(F[6], a, ms[6], undo[6]),
-                                    slice_bits(F[7], a, ms[7], undo[7]));
+                    v.x = pack_bf16(slice_bits(F[0], a, ms[0], undo_of(ms[0])),
+                                    slice_bits(F[1], a, ms[1], undo_of(ms[1])));
+                    v.y = pack_bf16(slice_bits(F[2], a, ms[2], undo_of(ms[2])),
+                                    slice_bits(F[3], a, ms[3], undo_of(ms[3])));
+                    v.z = pack_bf16(slice_bits(F[4], a, ms[4], undo_of(ms[4])),
+                                    slice_bits(F[5], a, ms[5], undo_of(ms[5])));
+                    v.w = pack_bf16(slice_bits(F[6], a, ms[6], undo_of(ms[6])),
+                                    slice_bits(F[7], a, ms[7], undo_of(ms[7])));
                     *reinterpret_cast<uint4*>(dst + a * S::kSliceStage) = v;
                 }
                 fence_async_smem();
@@ -578,14 +606,14 @@ k_oz_update(MB<const double> X, const double* __restrict__ C, MB<const double> Y
                                    (uint32_t)c0;
             long long V[QH];
 #pragma unroll
-            for (int k = 0; k < QH; k += 4) {
-                float g[kGroups][4];
+            for (int k = 0; k < QH; k += 2) {
+                float g[kGroups][2];
 #pragma unroll
                 for (int gi = 0; gi < kGroups; ++gi)
-                    tmem_ld4(taddr + (uint32_t)(gi * Q + k), g[gi]);
+                    tmem_ld2(taddr + (uint32_t)(gi * Q + k), g[gi]);
                 tmem_wait_ld();
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
+                for (int u = 0; u < 2; ++u) {
                     float gu[kGroups];
 #pragma unroll
                     for (int gi = 0; gi < kGroups; ++gi) gu[gi] = g[gi][u];
@@ -836,26 +864,24 @@ k_oz_gram(MB<const double> X, MB<const double> Y, int64_t n, double* __restrict_
                     const int cc = isxc[cb] ? cb * 32 + lane : cb * 32 + lane - P;
                     uint64_t F[8];
                     uint32_t ms[8];
-                    float undo[8];
 #pragma unroll
                     for (int u = 0; u < 8; ++u) {
                         const double x = (u < myrows) ? raw[u * wcol[cb]] : 0.0;
                         F[u] = fixed63(x, e[cb]);
                         const bool neg = (__double_as_longlong(x) >> 63) != 0;
                         ms[u] = sign_magic(neg);
-                        undo[u] = sign_undo(neg);
                     }
 #pragma unroll
                     for (int a = 0; a < kGSlices; ++a) {
                         uint4 v;
-                        v.x = pack_bf16(byte_slice_bits(F[0], a, ms[0], undo[0]),
-                                        byte_slice_bits(F[1], a, ms[1], undo[1]));
-                        v.y = pack_bf16(byte_slice_bits(F[2], a, ms[2], undo[2]),
-                                        byte_slice_bits(F[3], a, ms[3], undo[3]));
-                        v.z = pack_bf16(byte_slice_bits(F[4], a, ms[4], undo[4]),
-                                        byte_slice_bits(F[5], a, ms[5], undo[5]));
-                        v.w = pack_bf16(byte_slice_bits(F[6], a, ms[6], undo[6]),
-                                        byte_slice_bits(F[7], a, ms[7], undo[7]));
+                        v.x = pack_bf16(byte_slice_bits(F[0], a, ms[0], undo_of(ms[0])),
+                                        byte_slice_bits(F[1], a, ms[1], undo_of(ms[1])));
+                        v.y = pack_bf16(byte_slice_bits(F[2], a, ms[2], undo_of(ms[2])),
+                                        byte_slice_bits(F[3], a, ms[3], undo_of(ms[3])));
+                        v.z = pack_bf16(byte_slice_bits(F[4], a, ms[4], undo_of(ms[4])),
+                                        byte_slice_bits(F[5], a, ms[5], undo_of(ms[5])));
+                        v.w = pack_bf16(byte_slice_bits(F[6], a, ms[6], undo_of(ms[6])),
+                                        byte_slice_bits(F[7], a, ms[7], undo_of(ms[7])));
                         // X: slice a (0-based) in pair a / 2, rows 64 (a % 2) + cc, K-group
                         // par; Y: slice a is B rows a Q .. a Q + Q - 1
                         const int off =
@@ -959,22 +985,22 @@ k_oz_gram(MB<const double> X, MB<const double> Y, int64_t n, double* __restrict_
             // block j holds group j + 2 in the upper lanes and group j + 3 in the lower ones
             long long V[QH];
 #pragma unroll
-            for (int k = 0; k < QH; k += 4) {
-                float g[kGGroups][4];
+            for (int k = 0; k < QH; k += 2) {
+                float g[kGGroups][2];
                 if (upper) {
 #pragma unroll
                     for (int j = 0; j < kGGroups; ++j)
-                        tmem_ld4(taddr + (uint32_t)(j * Q + k), g[j]);
+                        tmem_ld2(taddr + (uint32_t)(j * Q + k), g[j]);
                 } else {
 #pragma unroll
-                    for (int u = 0; u < 4; ++u) g[0][u] = 0.f;
+                    for (int u = 0; u < 2; ++u) g[0][u] = 0.f;
 #pragma unroll
                     for (int j = 0; j + 1 < kGGroups; ++j)
-                        tmem_ld4(taddr + (uint32_t)(j * Q + k), g[j + 1]);
+                        tmem_ld2(taddr + (uint32_t)(j * Q + k), g[j + 1]);
                 }
                 tmem_wait_ld();
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
+                for (int u = 0; u < 2; ++u) {
                     float gu[kGGroups];
 #pragma unroll
                     for (int gi = 0; gi < kGGroups; ++gi) gu[gi] = g[gi][u];
