@@ -10,6 +10,7 @@ Usage: python tests/golden/make_oracle_counts.py [workload ...]   (ani3d, sky3d,
        python tests/golden/make_oracle_counts.py diff2d
        python tests/golden/make_oracle_counts.py --perturbed SEED diff2d   (target solve)
        python tests/golden/make_oracle_counts.py --perturbed SEED diff2d-forward | diff2d-adjoint
+       python tests/golden/make_oracle_counts.py --perturbed-hist SEED diff2d-target | diff2d-forward
 
 The diff2d form records the differentiable workload (2D diffusion 512^2, kappa = exp of a
 Gaussian random field, t = 16, s = 3): the solve for the target x* (field seed 5, b = 1),
@@ -22,6 +23,11 @@ from the given seed, and stores the iteration count under "<key>/perturbed/<SEED
 spread of these counts is the oracle's own sensitivity to rounding-level changes, which
 bounds how closely any other floating-point implementation can be expected to match the
 count.  Several seeds may run at once; each write takes an exclusive lock on the file.
+
+The --perturbed-hist form runs the first 21 s-step iterations of the differentiable
+workload's target or forward solve with the same perturbation of b and stores their
+residual norms under "<key>/perturbed_hist/<SEED>": the iteration from which the history
+itself is sensitive to rounding.
 """
 import json
 import os
@@ -93,6 +99,20 @@ def diff2d_perturbed(seed, which):
     key = f"diff2d/N{N}/t{t}/s{s}/sre/sstep/fp64/{which}/perturbed/{seed}"
     store(key, dict(iters=res.iters, status=res.status, seconds=round(time.time() - t0, 2)))
     print(key, res.iters, flush=True)
+
+
+def perturbed_hist(seed, which):
+    """First 21 residual norms of the differentiable workload's target (field seed 5) or
+    forward (field seed 4) solve, b = 1 multiplied entrywise by (1 + 1e-15 xi)."""
+    N, t, s = DIFF2D_N, DIFF2D_T, DIFF2D_S
+    lk = wl.kappa_gaussian_field2d(N, seed=5 if which == "target" else 4, corr=16.0)
+    A = wl.stencil_matrix((N, N), kappa=np.exp(lk))
+    part = wl.partition_boxes((N, N), t)
+    b = 1.0 + 1e-15 * np.random.default_rng(seed).standard_normal(N * N)
+    res = o.solve(A, b, part, t, s, tol=1e-8, maxit=20, variant="sre")
+    key = f"diff2d/N{N}/t{t}/s{s}/sre/sstep/fp64/{which}/perturbed_hist/{seed}"
+    store(key, dict(hist=[float(h) for h in res.hist[:21]]))
+    print(key, flush=True)
 
 
 def perturbed(seed, name):
@@ -175,6 +195,9 @@ def one_s(s, name):
 
 
 def main(names):
+    if names and names[0] == "--perturbed-hist":
+        perturbed_hist(int(names[1]), names[2].split("-")[1])
+        return
     if names and names[0] == "--perturbed":
         perturbed(int(names[1]), names[2])
         return

@@ -99,15 +99,25 @@ def test_differentiable_workload_full_size_against_oracle_record():
     """The differentiable configuration at its full size (512^2, kappa = exp of a Gaussian
     random field with correlation length 16, t = 16, s = 3, tol 1e-8): the solve for the
     target x* (field seed 5, b = 1), the forward solve x (field seed 4, b = 1), the adjoint
-    solve A lambda = x - x* and dL/dlog kappa, each against the oracle's whole-solve record
-    (tests/golden/oracle_counts.json, written by the oracle only): iteration counts within
-    the spread of oracle solves whose right-hand side was perturbed at the rounding level
-    (the counts are chaotic in rounding at this size), widened by one; the first 21
-    residual norms to 1e-6, the true relative residual, and x, lambda
-    and the gradient at 256 sampled rows (float64 tolerances relative to the max-norm of
-    the oracle's vector: 1e-8 for x*, x and lambda, 1e-7 for the gradient, a product of
-    two solutions)."""
+    solve A lambda = x - x* and dL/dlog kappa, against the oracle's records
+    (tests/golden/oracle_counts.json, written by the oracle only).
+
+    This workload is sensitive to rounding: with b multiplied by (1 + 1e-15 xi) the oracle's
+    own residual norms move by about 2e-6 at the third s-step iteration and by tens of
+    percent from the fourth ("perturbed_hist" records), and its iteration counts spread
+    ("perturbed" records).  So the bars are:
+    * iteration counts within the oracle's perturbation spread, widened by one;
+    * residual norm k within max(1e-6, twice the oracle's perturbation spread at k);
+    * the true relative residual <= 1.01e-8 (the solutions themselves are what is unique);
+    * x, x* and lambda at 256 sampled rows within the bound that any two solutions with
+      those residuals obey, |u - v| <= ||u - v||_2 <= (||r_u|| + ||r_v||) / lambda_min(A)
+      (lambda_min by shift-invert Lanczos), the adjoint's right-hand side difference
+      included;
+    * the gradient kernel at full size: the GPU's dL/dlog kappa equals the oracle's
+      formula applied to the GPU's own x and lambda (sampled rows, 1e-12 of the max-norm);
+    * the loss within the bound implied by the bounds on x - x*."""
     import json
+    from scipy.sparse.linalg import eigsh
     gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden",
                                        "oracle_counts.json")))
     key = "diff2d/N512/t16/s3/sre/sstep/fp64"
@@ -120,11 +130,24 @@ def test_differentiable_workload_full_size_against_oracle_record():
     S = ekcg.Solver(A, t, part, max_s=s)
     val = torch.empty(A.nnz, dtype=torch.float64, device="cuda")
     one = torch.ones(N * N, dtype=torch.float64, device="cuda")
+    rows = np.array(gold[key + "/grad_logkappa"]["rows"])
+
+    def lam_min(Amat):
+        return float(eigsh(Amat.to_scipy().tocsc(), k=1, sigma=0, which="LM",
+                           return_eigenvectors=False)[0])
 
     def spread(which):
         pre = f"{key}/{which}/perturbed/"
         return [gold[f"{key}/{which}"]["iters"]] + [v["iters"] for k, v in gold.items()
                                                     if k.startswith(pre)]
+
+    def hist_tol(which):
+        base = np.array(gold[f"{key}/{which}"]["hist"][:21])
+        pre = f"{key}/{which}/perturbed_hist/"
+        pert = [np.array(v["hist"][:21]) for k, v in gold.items() if k.startswith(pre)]
+        assert len(pert) >= 2, which
+        dev = np.max([np.abs(h - base) / base for h in pert], axis=0)
+        return base, np.maximum(1e-6, 2.0 * dev)
 
     def solve(log_k, rhs, which, Amat, rhs_np):
         rec = gold[f"{key}/{which}"]
@@ -134,25 +157,43 @@ def test_differentiable_workload_full_size_against_oracle_record():
         x, it, hist, st = S.solve(rhs, s=s, tol=1e-8, maxit=5000)
         counts = spread(which)
         assert st == 0 and min(counts) - 1 <= it <= max(counts) + 1, (it, counts)
-        np.testing.assert_allclose(hist[:21], rec["hist"][:21], rtol=1e-6)
         xh = x.cpu().numpy()
-        assert (np.linalg.norm(rhs_np - Amat.to_scipy() @ xh) <= 1.01e-8 *
-                np.linalg.norm(rhs_np))
-        ref = np.array(rec["x"]["values"])
-        rows = np.array(gold[key + "/grad_logkappa"]["rows"])
-        assert np.max(np.abs(xh[rows] - ref)) <= 1e-8 * rec["x"]["norminf"]
-        return x, xh
+        res = float(np.linalg.norm(rhs_np - Amat.to_scipy() @ xh))
+        assert res <= 1.01e-8 * np.linalg.norm(rhs_np)
+        return x, xh, np.array(hist), res
 
-    xs, xsh = solve(lk_star, one, "target", A_star, np.ones(N * N))
-    x, xh = solve(lk, one, "forward", A, np.ones(N * N))
+    # target and forward: histories against the oracle's perturbation spread
+    lmin_star, lmin = lam_min(A_star), lam_min(A)
+    xs, xsh, hs, res_s = solve(lk_star, one, "target", A_star, np.ones(N * N))
+    x, xh, hx, res_x = solve(lk, one, "forward", A, np.ones(N * N))
+    for which, h in (("target", hs), ("forward", hx)):
+        base, tol = hist_tol(which)
+        m = min(len(h), len(base))
+        assert np.all(np.abs(h[:m] - base[:m]) <= tol[:m] * base[:m]), (which, h[:m], base[:m])
+    nb = float(np.sqrt(N * N))
+    bound_s = (res_s + gold[key + "/target"]["relres"] * nb) / lmin_star
+    bound_x = (res_x + gold[key + "/forward"]["relres"] * nb) / lmin
+    assert np.max(np.abs(xsh[rows] - np.array(gold[key + "/target"]["x"]["values"]))) <= bound_s
+    assert np.max(np.abs(xh[rows] - np.array(gold[key + "/forward"]["x"]["values"]))) <= bound_x
+    # adjoint: its right-hand side is the GPU's x - x*, within bound_x + bound_s of the
+    # oracle's (whose norm is sqrt(2 loss))
     g = x - xs
-    lam, lamh = solve(lk, g.contiguous(), "adjoint", A, g.cpu().numpy())
+    gh = g.cpu().numpy()
+    dg = bound_x + bound_s
+    loss_o = gold[key + "/grad_logkappa"]["loss"]
+    ng_o = np.sqrt(2.0 * loss_o)
+    lam, lamh, hl, res_l = solve(lk, g.contiguous(), "adjoint", A, gh)
+    assert abs(hl[0] - gold[key + "/adjoint"]["hist"][0]) <= dg + 1e-6 * hl[0]
+    bound_l = (res_l + gold[key + "/adjoint"]["relres"] * ng_o + dg) / lmin
+    assert np.max(np.abs(lamh[rows] - np.array(gold[key + "/adjoint"]["x"]["values"]))) <= bound_l
+    # the gradient kernel at full size, on the GPU's own lambda and x
     glk = torch.empty(N * N, dtype=torch.float64, device="cuda")
     ekcg.ekcg_diffusion2d_grad_logkappa(S.ctx, N, N, 1.0, 1.0,
                                         torch.as_tensor(lk.ravel(), device="cuda"), lam, x, glk)
-    rec = gold[key + "/grad_logkappa"]
-    rows = np.array(rec["rows"])
-    got = glk.cpu().numpy()[rows]
-    assert np.max(np.abs(got - np.array(rec["values"]))) <= 1e-7 * rec["norminf"]
-    np.testing.assert_allclose(0.5 * float((g * g).sum()), rec["loss"], rtol=1e-7)
+    ref = o.diffusion2d_grad_logkappa(lk.ravel(), N, N, lamh, xh)
+    got = glk.cpu().numpy()
+    assert np.max(np.abs(got[rows] - ref[rows])) <= 1e-12 * np.max(np.abs(ref))
+    # the loss 0.5 ||g||^2 against the oracle's
+    ng = float(np.linalg.norm(gh))
+    assert abs(0.5 * ng * ng - loss_o) <= (ng + 0.5 * dg) * dg + 1e-12 * loss_o
     S.close()
