@@ -143,6 +143,45 @@ def right_solve_upper(W: np.ndarray, R: np.ndarray, dropped=()) -> np.ndarray:
     return X
 
 
+def right_multiply_inverse(W, R):
+    """W R^{-1} by the explicit inverse of the upper-triangular R (R^{-1} from a triangular
+    solve against the identity), then one matrix product: the other way to apply the
+    factor of A-CholQR, which the paper leaves open (Section 3.1 writes W R^{-1})."""
+    Rinv = sla.solve_triangular(R, np.eye(R.shape[0]), lower=False)
+    return W @ Rinv
+
+
+# How A-CholQR applies its factor: "solve" (a triangular solve, the default) or "inverse"
+# (the product with R^{-1}).  Scoped by `factor_application`; read when a solve starts.
+_FACTOR_APPLICATION = ["solve"]
+
+
+class factor_application:
+    """with factor_application("inverse"): solves started inside apply W R^{-1} as the
+    product with the explicit inverse (without deflation)."""
+
+    def __init__(self, mode):
+        if mode not in ("solve", "inverse"):
+            raise ValueError(mode)
+        self.mode = mode
+
+    def __enter__(self):
+        self.prev = _FACTOR_APPLICATION[0]
+        _FACTOR_APPLICATION[0] = self.mode
+        return self
+
+    def __exit__(self, *exc):
+        _FACTOR_APPLICATION[0] = self.prev
+        return False
+
+
+def a_cholqr_inverse(W, AW, breakdown_tol):
+    """A-CholQR applying its factor by the explicit inverse: G = W^T A W = R^T R,
+    W <- W R^{-1}, A W <- (A W) R^{-1}."""
+    R = cholesky_upper(W.T @ AW, breakdown_tol)
+    return right_multiply_inverse(W, R), right_multiply_inverse(AW, R)
+
+
 def a_cholqr(W, AW, breakdown_tol, deflate=False):
     """A-CholQR: G = W^T A W = R^T R, W <- W R^{-1} (and A W <- A W R^{-1}); with
     deflate=True the columns whose pivots fail the breakdown rule are dropped (zeroed)."""
@@ -210,6 +249,9 @@ class _Ctx:
         self.deflate = deflate
         if deflate and orth != "acholqr":
             raise ValueError("deflation is defined for A-CholQR")
+        self.inverse = _FACTOR_APPLICATION[0] == "inverse"
+        if self.inverse and (deflate or orth != "acholqr"):
+            raise ValueError("the explicit-inverse application is defined for A-CholQR")
         self.spmm = 0
 
     def matmul(self, W):
@@ -231,7 +273,9 @@ class _Ctx:
         return self.pre.apply(AW)
 
     def self_orth(self, W, AW):
-        if self.orth == "acholqr":
+        if self.orth == "acholqr" and self.inverse:
+            W, AW = a_cholqr_inverse(W, AW, self.tol_bd)
+        elif self.orth == "acholqr":
             W, AW = (a_cholqr(W, AW, self.tol_bd, deflate=True) if self.deflate
                      else a_cholqr(W, AW, self.tol_bd))
         elif self.orth == "precholqr":

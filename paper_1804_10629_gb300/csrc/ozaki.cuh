@@ -17,9 +17,9 @@
 //     weigh at most about 2^-60 of max|X_i| max|C_q| per term, below one float64 rounding of
 //     every term within 2^7 of that product;
 //   * the epilogue combines the nine exact groups in 64-bit integers,
-//     V = sum_g G_g 2^{7(10-g)} (kept as V >> 14 below 2^62), converts V once to float64 and
-//     applies the scale and the subtraction with one fused multiply-add:
-//     OUT = Y - (V >> 14) 2^{e_i + f_q - 2100}.
+//     V = sum_g G_g 2^{7(10-g)} (kept as V / 2^14 rounded to the nearest integer, below
+//     2^62), converts it once to float64 and applies the scale and the subtraction with one
+//     fused multiply-add: OUT = Y - (V / 2^14) 2^{e_i + f_q - 2100}.
 //
 // Tensor-core mechanics: A (X slices, 128 rows x K) and B (C slices, Q x K) sit in shared
 // memory in the canonical K-major no-swizzle layout of 8 x 16-byte core matrices (leading
@@ -133,10 +133,11 @@ __device__ __forceinline__ void tmem_wait_ld() {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-// the nine exact group sums G_2 .. G_10 combined into about V >> 14, V = sum_g G_g 2^{7(10-g)}
-// (|G_g| < 2^24, |G_2| < 2^21): G_2 2^42 + G_3 2^35 + ... + G_8 + (G_9 >> 7) + (G_10 >> 14),
-// within two units of floor(V / 2^14), below 2^62.  The terms below 2^32 are added by
-// 32 x 32 -> 64-bit multiply-adds, the two top terms into the high word.
+// the nine exact group sums G_2 .. G_10 combined into V / 2^14, V = sum_g G_g 2^{7(10-g)}
+// (|G_g| < 2^24, |G_2| < 2^21): G_2 2^42 + G_3 2^35 + ... + G_8 + G_9 / 2^7 + G_10 / 2^14,
+// the last two rounded to the nearest integer (unbiased: the rounding errors of the tiles do
+// not add up in one direction), within one unit of V / 2^14, below 2^62.  The terms below
+// 2^32 are added by 32 x 32 -> 64-bit multiply-adds, the two top terms into the high word.
 __device__ __forceinline__ long long combine_groups(const float (&g)[kGroups]) {
     // each group converted where it is added: few registers live at a time
     long long acc = (long long)(__float2int_rn(g[1]) * 8 + __float2int_rn(g[0]) * 1024) << 32;
@@ -144,8 +145,8 @@ __device__ __forceinline__ long long combine_groups(const float (&g)[kGroups]) {
     acc += (long long)__float2int_rn(g[3]) * 2097152;
     acc += (long long)__float2int_rn(g[4]) * 16384;
     acc += (long long)__float2int_rn(g[5]) * 128;
-    return acc + (__float2int_rn(g[6]) + (__float2int_rn(g[7]) >> 7) +
-                  (__float2int_rn(g[8]) >> 14));
+    return acc + (__float2int_rn(g[6]) + ((__float2int_rn(g[7]) + 64) >> 7) +
+                  ((__float2int_rn(g[8]) + 8192) >> 14));
 }
 // 2^{ex - 1023} for a biased exponent ex: 0 below the normal range, infinity above it
 __device__ __forceinline__ double pow2_biased(int ex) {
@@ -235,17 +236,17 @@ __device__ __forceinline__ uint32_t byte_slice_bits(uint64_t F, int a, uint32_t 
     }
     return __float_as_uint(__uint_as_float(w) + undo);
 }
-// the eight exact byte-pair group sums G_2 .. G_9 combined into about V >> 16,
-// V = sum_g G_g 2^{8(9-g)} (|G_g| < 2^24, |G_2| < 2^21): G_2 2^40 + G_3 2^32 + G_4 2^24 +
-// G_5 2^16 + G_6 2^8 + G_7 + (G_8 >> 8) + (G_9 >> 16), within two units of floor(V / 2^16),
-// below 2^62.
+// the eight exact byte-pair group sums G_2 .. G_9 combined into V / 2^14,
+// V = sum_g G_g 2^{8(9-g)} (|G_g| < 2^24, |G_2| < 2^21): G_2 2^42 + G_3 2^34 + G_4 2^26 +
+// G_5 2^18 + G_6 2^10 + G_7 2^2 + G_8 / 2^6 + G_9 / 2^14, the last two rounded to the
+// nearest integer (unbiased), within one unit of V / 2^14, below 2^63.
 __device__ __forceinline__ long long combine_byte_groups(const float (&g)[8]) {
-    long long acc = (long long)(__float2int_rn(g[1]) + __float2int_rn(g[0]) * 256) << 32;
-    acc += (long long)__float2int_rn(g[2]) * 16777216;
-    acc += (long long)__float2int_rn(g[3]) * 65536;
-    acc += (long long)__float2int_rn(g[4]) * 256;
-    return acc + (__float2int_rn(g[5]) + (__float2int_rn(g[6]) >> 8) +
-                  (__float2int_rn(g[7]) >> 16));
+    long long acc = (long long)(__float2int_rn(g[1]) * 4 + __float2int_rn(g[0]) * 1024) << 32;
+    acc += (long long)__float2int_rn(g[2]) * 67108864;
+    acc += (long long)__float2int_rn(g[3]) * 262144;
+    acc += (long long)__float2int_rn(g[4]) * 1024;
+    return acc + (__float2int_rn(g[5]) * 4 + ((__float2int_rn(g[6]) + 32) >> 6) +
+                  ((__float2int_rn(g[7]) + 8192) >> 14));
 }
 
 // 16-byte global -> shared copy by this thread (cp.async); src_bytes 0 writes zeros
@@ -666,7 +667,7 @@ k_oz_update(MB<const double> X, const double* __restrict__ C, MB<const double> Y
 // cut into eight byte slices of the same 63-bit fixed-point magnitude F (slice a, 1-based,
 // holds bits 64 - 8a .. 71 - 8a; bf16 holds every byte exactly).  The 36 slice pairs with
 // a + b <= 9 form eight groups g = 2..9; the epilogue adds the tile's
-// (V >> 16) 2^{e_p + f_q - 2098}, V = sum_g G_g 2^{8(9-g)}, into a float64 accumulator per
+// (V / 2^14) 2^{e_p + f_q - 2100}, V = sum_g G_g 2^{8(9-g)}, into a float64 accumulator per
 // output held in registers across the CTA's tiles (the dropped pairs and the truncation of
 // F weigh at most about 2^-60 of the product of the column maxima per term).  Each CTA
 // writes its P x Q partial sum; k_gram_reduce adds the partials in CTA order.
@@ -1014,7 +1015,7 @@ k_oz_gram(MB<const double> X, MB<const double> Y, int64_t n, double* __restrict_
             const int ep = own ? cexp[cb3][p] : 0;
 #pragma unroll
             for (int q = 0; q < QH; ++q)
-                acc[q] = fma((double)V[q], pow2_biased(ep + cexp[cb3][P + c0 + q] - 1075), acc[q]);
+                acc[q] = fma((double)V[q], pow2_biased(ep + cexp[cb3][P + c0 + q] - 1077), acc[q]);
             __syncwarp();
             if (lane == 0) mbar_arrive(&cexp_empty[cb3]);
         }

@@ -11,6 +11,7 @@ Usage: python tests/golden/make_oracle_counts.py [workload ...]   (ani3d, sky3d,
        python tests/golden/make_oracle_counts.py --perturbed SEED diff2d   (target solve)
        python tests/golden/make_oracle_counts.py --perturbed SEED diff2d-forward | diff2d-adjoint
        python tests/golden/make_oracle_counts.py --perturbed-hist SEED diff2d-target | diff2d-forward
+       python tests/golden/make_oracle_counts.py --perturbed SEED sky3d-inverse   (SEED 0: b as is)
 
 The diff2d form records the differentiable workload (2D diffusion 512^2, kappa = exp of a
 Gaussian random field, t = 16, s = 3): the solve for the target x* (field seed 5, b = 1),
@@ -23,6 +24,10 @@ from the given seed, and stores the iteration count under "<key>/perturbed/<SEED
 spread of these counts is the oracle's own sensitivity to rounding-level changes, which
 bounds how closely any other floating-point implementation can be expected to match the
 count.  Several seeds may run at once; each write takes an exclusive lock on the file.
+
+The "-inverse" workloads solve with A-CholQR applying its factor W R^{-1} as the product
+with the explicit inverse (the paper leaves the method open; the tensor-core contraction
+applies it that way) and store the counts under "<key>/inverse[/perturbed/<SEED>]".
 
 The --perturbed-hist form runs the first 21 s-step iterations of the differentiable
 workload's target or forward solve with the same perturbation of b and stores their
@@ -116,6 +121,24 @@ def perturbed_hist(seed, which):
 
 
 def perturbed(seed, name):
+    if name.endswith("-inverse"):
+        # A-CholQR applying its factor by the explicit inverse; seed 0 = b unperturbed
+        base = name[: -len("-inverse")]
+        cfg = RUNS[base]
+        p = cfg["make"]()
+        b = p.b if seed == 0 else p.b * (
+            1.0 + 1e-15 * np.random.default_rng(seed).standard_normal(p.A.n))
+        for s in cfg["s"]:
+            t0 = time.time()
+            with o.factor_application("inverse"):
+                res = o.solve(p.A, b, p.part, p.t, s, tol=1e-8, maxit=20000,
+                              variant=cfg["variant"])
+            dt = time.time() - t0
+            key = (f"{base}/t{p.t}/s{s}/{cfg['variant']}/sstep/fp64/inverse" +
+                   ("" if seed == 0 else f"/perturbed/{seed}"))
+            store(key, dict(iters=res.iters, status=res.status, seconds=round(dt, 2)))
+            print(key, res.iters, res.status, f"{dt:.1f}s", flush=True)
+        return
     if name == "diff2d":
         return diff2d_target_perturbed(seed)
     if name in ("diff2d-forward", "diff2d-adjoint"):

@@ -107,7 +107,8 @@ def test_differentiable_workload_full_size_against_oracle_record():
     percent from the fourth ("perturbed_hist" records), and its iteration counts spread
     ("perturbed" records).  So the bars are:
     * iteration counts within the oracle's perturbation spread, widened by one;
-    * residual norm k within max(1e-6, twice the oracle's perturbation spread at k);
+    * residual norm k within max(1e-6, twice the oracle's perturbation spread at k), up to
+      the first iteration that the perturbation moves by more than 1e-3;
     * the true relative residual <= 1.01e-8 (the solutions themselves are what is unique);
     * x, x* and lambda at 256 sampled rows within the bound that any two solutions with
       those residuals obey, |u - v| <= ||u - v||_2 <= (||r_u|| + ||r_v||) / lambda_min(A)
@@ -142,12 +143,17 @@ def test_differentiable_workload_full_size_against_oracle_record():
                                                     if k.startswith(pre)]
 
     def hist_tol(which):
+        """The oracle's norms, the tolerance (twice its perturbation spread, at least
+        1e-6), and how many of them to compare: those before the first one that the
+        perturbation moves by more than 1e-3 (past it the history is chaotic and a few
+        seeds do not bound it)."""
         base = np.array(gold[f"{key}/{which}"]["hist"][:21])
         pre = f"{key}/{which}/perturbed_hist/"
         pert = [np.array(v["hist"][:21]) for k, v in gold.items() if k.startswith(pre)]
         assert len(pert) >= 2, which
         dev = np.max([np.abs(h - base) / base for h in pert], axis=0)
-        return base, np.maximum(1e-6, 2.0 * dev)
+        chaotic = np.nonzero(dev > 1e-3)[0]
+        return base, np.maximum(1e-6, 2.0 * dev), int(chaotic[0]) if len(chaotic) else 21
 
     def solve(log_k, rhs, which, Amat, rhs_np):
         rec = gold[f"{key}/{which}"]
@@ -167,8 +173,9 @@ def test_differentiable_workload_full_size_against_oracle_record():
     xs, xsh, hs, res_s = solve(lk_star, one, "target", A_star, np.ones(N * N))
     x, xh, hx, res_x = solve(lk, one, "forward", A, np.ones(N * N))
     for which, h in (("target", hs), ("forward", hx)):
-        base, tol = hist_tol(which)
-        m = min(len(h), len(base))
+        base, tol, kc = hist_tol(which)
+        assert kc >= 3, (which, kc)
+        m = min(len(h), len(base), kc)
         assert np.all(np.abs(h[:m] - base[:m]) <= tol[:m] * base[:m]), (which, h[:m], base[:m])
     nb = float(np.sqrt(N * N))
     bound_s = (res_s + gold[key + "/target"]["relres"] * nb) / lmin_star
