@@ -162,9 +162,10 @@ int ekcg_last_stats(const ekcg_ctx* ctx, int64_t* kernel_launches, int64_t* spmm
  * [0, nblocks), natural row order, copied), each diagonal block factored by incomplete
  * Cholesky with zero fill-in, computed on the host in the library's row order (within a
  * block the natural order).  Every block must lie inside one of the t domains (the paper's
- * blocks are subdomains of the t domains).  The s-step solves then build the first block as
- * L^{-T} T(L^{-1} r) and every later candidate as M^{-1} A W_{j-1}.  bpart = NULL removes
- * the preconditioner.  Float64 precision and the s-step basis (EKCG_SSTEP) only.
+ * blocks are subdomains of the t domains).  The solves then build the first block as
+ * L^{-T} T(L^{-1} r) and every later candidate as M^{-1} A W_{j-1}; in the CA bases every
+ * power M^{-1} A W_{j+i-1} as well.  bpart = NULL removes the preconditioner.  Float64
+ * precision; the s-step or a CA basis (EKCG_SSTEP, EKCG_CA5, EKCG_CA7).
  * Errors: EKCG_EINVAL (ids out of range, a block across two domains, IC(0) breakdown,
  * other precision or basis), EKCG_ENOMEM, EKCG_ECUDA.                                    */
 int ekcg_set_block_jacobi(ekcg_ctx* ctx, const int32_t* bpart, int nblocks);

@@ -1040,12 +1040,17 @@ struct Engine {
             q0 = 0;
             qc = (int)j0;
         }
-        // first block W_j: T(r_{k-1}) (MSDO), T(r_0) (k = 1) or A W_{j-1}
+        // first block W_j: T(r_{k-1}) (MSDO), T(r_0) (k = 1) or A W_{j-1}; with the block
+        // Jacobi preconditioner L^{-T} T(L^{-1} r) and M^{-1} A W_{j-1} (Section 5)
         const T* cand = nullptr;
+        const bool pre = c->bj_nblk > 0;
         if (v == EKCG_MSDO) {
-            EK_TRY(run_split<T>(c, r, W(j0)));
+            EK_TRY(first_block(r, W(j0)));
         } else if (k == 1) {
-            EK_TRY(run_split<T>(c, r0_for_T, W(j0)));
+            EK_TRY(first_block(r0_for_T, W(j0)));
+        } else if (pre) {
+            EK_TRY(run_copy<T>(c, W(j0), Z(j0 - 1), slot));
+            EK_TRY(precondition(W(j0)));
         } else {
             cand = Z(j0 - 1);
         }
@@ -1060,10 +1065,11 @@ struct Engine {
         } else if (cand) {
             EK_TRY(run_copy<T>(c, W(j0), cand, slot));
         }
-        // powers W_{j+i} = A W_{j+i-1}
+        // powers W_{j+i} = A W_{j+i-1} (preconditioned: M^{-1} A W_{j+i-1})
         for (int i = 1; i < s; ++i) {
             const int64_t j = j0 + i;
             EK_TRY(run_copy<T>(c, W(j), Z(j - 1), slot));
+            if (pre) EK_TRY(precondition(W(j)));
             EK_TRY(run_spmm<T>(c, W(j), Z(j), t));
         }
         if (k > 1) EK_TRY(cgs2(j0, s, q0, qc, nullptr));
@@ -2029,9 +2035,9 @@ int ekcg_set_block_jacobi(ekcg_ctx* c, const int32_t* bpart, int nblocks) {
     EK_CUDA(cudaStreamSynchronize(c->stream));
     free_block_jacobi(c);
     if (!bpart) return EKCG_OK;
-    if (nblocks < 1 || c->opts.precision != EKCG_FP64 || c->opts.basis != EKCG_SSTEP) {
+    if (nblocks < 1 || c->opts.precision != EKCG_FP64 || c->opts.basis == EKCG_RESTRUCT) {
         set_error("ekcg_set_block_jacobi",
-                  "needs nblocks >= 1, float64 precision and the s-step basis");
+                  "needs nblocks >= 1, float64 precision and the s-step or a CA basis");
         return EKCG_EINVAL;
     }
     const int64_t n = c->n;

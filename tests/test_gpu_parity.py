@@ -162,14 +162,18 @@ def test_restructured_msdo_is_rejected():
 
 @pytest.mark.parametrize("variant", ["sre", "sre2", "msdo"])
 @pytest.mark.parametrize("s", [1, 2])
-def test_block_jacobi_parity(variant, s):
-    """Split preconditioned s-step forms (Algorithms 8-10) with block Jacobi IC(0) over 16
-    boxes inside the 4 domains, against the oracle (its own IC(0) and triangular solves)."""
+@pytest.mark.parametrize("basis", ["sstep", "ca5", "ca7"])
+def test_block_jacobi_parity(variant, s, basis):
+    """Split preconditioned s-step and CA forms (Section 5, Algorithms 8-10; in the CA
+    forms every power M^{-1} A W) with block Jacobi IC(0) over 16 boxes inside the 4
+    domains, against the oracle (its own IC(0) and triangular solves)."""
     A, b, part = ragged_problem()
     bpart = wl.partition_boxes((45, 37), 16)
     M = o.BlockJacobi(A, bpart, "ic0")
-    ref = o.solve(A, b, part, 4, s, tol=1e-8, maxit=2000, variant=variant, precond=M)
-    S = ekcg.Solver(A, 4, part, variant=variant, max_s=s, max_basis_bytes=8 << 30)
+    ref = o.solve(A, b, part, 4, s, tol=1e-8, maxit=2000, variant=variant, basis=basis,
+                  precond=M)
+    S = ekcg.Solver(A, 4, part, variant=variant, basis=basis, max_s=s,
+                    max_basis_bytes=8 << 30)
     S.set_block_jacobi(bpart)
     x, it, hist, st = S.solve(dev(b), s=s, tol=1e-8, maxit=2000)
     x = x.cpu().numpy()
@@ -197,6 +201,10 @@ def test_block_jacobi_rejections():
     with pytest.raises(ekcg.EkcgError):
         F.set_block_jacobi(wl.partition_boxes((45, 37), 16))
     F.close()
+    R = ekcg.Solver(A, 4, part, basis="restructured", max_s=2)
+    with pytest.raises(ekcg.EkcgError):
+        R.set_block_jacobi(wl.partition_boxes((45, 37), 16))
+    R.close()
 
 
 @pytest.mark.parametrize("variant", ["sre", "sre2", "msdo"])
