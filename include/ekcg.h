@@ -197,7 +197,8 @@ int ekcg_wait_selftest(long long limit_cycles, void* stream);
  * outputs), EKCG_ENOMEM, EKCG_ECUDA.                                                      */
 int ekcg_fp64_fma_rate(void* stream, int* num_sms, double* tflops);
 
-/* Columns dropped by the rank-revealing A-CholQR (opts.deflate) in the last solve.        */
+/* Columns dropped by the rank-revealing A-CholQR (opts.deflate) in the last solve.
+ * Errors: EKCG_EINVAL (NULL arguments).                                                  */
 int ekcg_deflation_stats(const ekcg_ctx* ctx, int64_t* columns);
 
 /* Device-side convergence test (the `while` line of Algorithms 3 and 4) for later solves of
@@ -206,13 +207,15 @@ int ekcg_deflation_stats(const ekcg_ctx* ctx, int64_t* columns);
  * graph of conditional iterations: a one-thread kernel after each iteration compares
  * ||r_k|| with tol ||r_0||, checks k against maxit and the breakdown / timeout status word,
  * appends ||r_k|| to a device history and enables the next iteration; the host
- * synchronises once per batch of up to eight iterations and copies the history at the end.
+ * synchronises once per graph launch (a batch of B iterations, B a multiple of the period
+ * of the basis ring slots and at least 8) and copies the history at the end.
  * The kernels, their order and their arguments are those of the host-driven loop, so
  * results are bitwise the same.  Per-launch profiling (ekcg_set_profile) and the other
  * variants, bases and precisions use the host loop.  Errors: EKCG_EINVAL (NULL ctx).       */
 int ekcg_set_device_loop(ekcg_ctx* ctx, int on);
 
-/* Iterations of the last solve that ran in the device loop (0: the host loop ran all).     */
+/* Iterations of the last solve that ran in the device loop (0: the host loop ran all).
+ * Errors: EKCG_EINVAL (NULL arguments).                                                  */
 int ekcg_device_loop_stats(const ekcg_ctx* ctx, int64_t* device_iters);
 
 /* Turn the per-launch CUDA-event timing of later solves on (on != 0) or off, whatever
