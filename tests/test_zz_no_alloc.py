@@ -54,3 +54,33 @@ def test_noalloc_gram_rejects_sizes_beyond_its_scratch():
     st = ekcg.lib().ekcg_gram_noalloc(10, X.data_ptr(), 65, X.data_ptr(), 1, C.data_ptr(),
                                       None)
     assert st == ekcg.EKCG_EINVAL
+
+
+def test_noalloc_gram_captures_into_a_cuda_graph_and_allocates_nothing():
+    """After one warm-up call (which looks up the scratch address), a call changes the
+    device's free memory by nothing, and the call captured into a CUDA graph replays
+    correctly on new contents of X and Y."""
+    n, p, q = 3000, 32, 16
+    gen = torch.Generator(device="cuda").manual_seed(5)
+    X = torch.randn(n, p, dtype=torch.float64, device="cuda", generator=gen)
+    Y = torch.randn(n, q, dtype=torch.float64, device="cuda", generator=gen)
+    C = torch.empty(p * q, dtype=torch.float64, device="cuda")
+    ekcg.ekcg_gram_noalloc(n, X, p, Y, q, C)
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    ekcg.ekcg_gram_noalloc(n, X, p, Y, q, C)
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        ekcg.ekcg_gram_noalloc(n, X, p, Y, q, C)
+    for _ in range(2):
+        X.copy_(torch.randn(n, p, dtype=torch.float64, device="cuda", generator=gen))
+        Y.copy_(torch.randn(n, q, dtype=torch.float64, device="cuda", generator=gen))
+        C.fill_(float("nan"))
+        g.replay()
+        torch.cuda.synchronize()
+        Xh, Yh = X.cpu().numpy(), Y.cpu().numpy()
+        bound = n * 2.2e-16 * (np.abs(Xh).T @ np.abs(Yh))
+        got = C.cpu().numpy().reshape(p, q)
+        assert np.all(np.abs(got - Xh.T @ Yh) <= bound)
