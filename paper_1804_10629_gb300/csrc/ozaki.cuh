@@ -258,8 +258,9 @@ __device__ __forceinline__ void cp_async16_zfill(void* dst, const void* src, uin
 
 // ---- the update -------------------------------------------------------------------------
 // One persistent CTA per SM, warp-specialised:
-//   warps 0-7  (slicers): per 128-row tile, load the tile's X values (each thread half a row,
-//              P/2 values), take the row binade, and cut the values into the nine slices,
+//   warps 0-7  (slicers): per 128-row tile, take the tile's X values (each thread half a row,
+//              P/2 values, copied one tile ahead with cp.async into the thread's own
+//              shared chunks), take the row binade, and cut the values into the nine slices,
 //              one K-step (16 columns) at a time, into a ring of kStages shared stages;
 //   warp 8     (MMA): per K-step one thread issues one MMA per X slice a, against the C
 //              slices 1 .. 10 - a stacked along N (N = (10 - a) Q, in pieces of <= 256),
@@ -267,11 +268,12 @@ __device__ __forceinline__ void cp_async16_zfill(void* dst, const void* src, uin
 //              group a + b; one of kSets tensor-memory accumulator sets (two when 2 x 9 Q
 //              columns fit in 512); each stage is committed back to the slicers and each
 //              finished tile to the epilogue;
-//   warps 9-12 (epilogue): lane quarter w % 4 reads its 32 rows of the finished set,
-//              combines the nine groups, applies scale and subtraction and writes OUT;
-//   warp 13    (prefetch): while the slicers start tile k it asks L2 for the X and Y rows
-//              of tile k + 2 (bulk prefetches), so the slicers' and the epilogue's loads
-//              find their rows in L2 and HBM streams without gaps.
+//   warp 9     (prefetch): while the slicers start tile k it asks L2 for the X and Y rows
+//              of tile k + 2 (bulk prefetches), so the slicers' copies and the epilogue's
+//              loads find their rows in L2 and HBM streams without gaps;
+//   warps 10-17 (epilogue): warp w reads lane quarter w % 4 (32 rows) of the finished set
+//              for half of the Q columns ((w - 10) / 4), combines the nine groups, releases
+//              the accumulator set, then applies scale and subtraction and writes OUT.
 // mbarriers: full[s] / empty[s] per ring stage, acc_full[b] / acc_empty[b] and
 // erow_full[b] per accumulator set.  Each wait is bounded; a wait that runs out sets a
 // shared abort word that every role checks, so all roles leave their loops.
