@@ -12,6 +12,7 @@ Usage: python tests/golden/make_oracle_counts.py [workload ...]   (ani3d, sky3d,
        python tests/golden/make_oracle_counts.py --perturbed SEED diff2d-forward | diff2d-adjoint
        python tests/golden/make_oracle_counts.py --perturbed-hist SEED diff2d-target | diff2d-forward
        python tests/golden/make_oracle_counts.py --perturbed SEED sky3d-inverse   (SEED 0: b as is)
+       python tests/golden/make_oracle_counts.py --contraction-noise SEED sky3d
 
 The diff2d form records the differentiable workload (2D diffusion 512^2, kappa = exp of a
 Gaussian random field, t = 16, s = 3): the solve for the target x* (field seed 5, b = 1),
@@ -120,6 +121,43 @@ def perturbed_hist(seed, which):
     print(key, flush=True)
 
 
+def contraction_noise(seed, name):
+    """The workload solved with b as is, but with the block inner products of the
+    A-orthonormalisation (the CGS coefficients Q^T (A W) and the A-CholQR Gram W^T (A W))
+    each given an error of the size a float64 dot product may have, u (|X|^T |Y|) xi with
+    u = 2^-53 and xi uniform in (-1, 1) from the seed: what any float64-accurate
+    implementation of those contractions with another rounding may produce.  Stores the
+    iteration count under "<key>/contraction_noise/<SEED>"."""
+    cfg = RUNS[name]
+    p = cfg["make"]()
+    rng = np.random.default_rng(1000 + seed)
+    u = 2.0 ** -53
+
+    def noisy(X, Y):
+        return X.T @ Y + u * rng.uniform(-1.0, 1.0, (X.shape[1], Y.shape[1])) * (
+            np.abs(X).T @ np.abs(Y))
+
+    def a_cholqr_noisy(W, AW, breakdown_tol, deflate=False):
+        R = o.cholesky_upper(noisy(W, AW), breakdown_tol)
+        return o.right_solve_upper(W, R), o.right_solve_upper(AW, R)
+
+    def cgs2_noisy(W, AW, Q, matmul):
+        for _ in range(2):
+            W = W - Q @ noisy(Q, AW)
+            AW = matmul(W)
+        return W, AW
+
+    o.a_cholqr = a_cholqr_noisy          # this process only: the solver's A-CholQR and CGS2
+    o.cgs2_against = cgs2_noisy
+    for s in cfg["s"]:
+        t0 = time.time()
+        res = o.solve(p.A, p.b, p.part, p.t, s, tol=1e-8, maxit=20000, variant=cfg["variant"])
+        dt = time.time() - t0
+        key = f"{name}/t{p.t}/s{s}/{cfg['variant']}/sstep/fp64/contraction_noise/{seed}"
+        store(key, dict(iters=res.iters, status=res.status, seconds=round(dt, 2)))
+        print(key, res.iters, res.status, f"{dt:.1f}s", flush=True)
+
+
 def perturbed(seed, name):
     if name.endswith("-inverse"):
         # A-CholQR applying its factor by the explicit inverse; seed 0 = b unperturbed
@@ -218,6 +256,9 @@ def one_s(s, name):
 
 
 def main(names):
+    if names and names[0] == "--contraction-noise":
+        contraction_noise(int(names[1]), names[2])
+        return
     if names and names[0] == "--perturbed-hist":
         perturbed_hist(int(names[1]), names[2].split("-")[1])
         return
